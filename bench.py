@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Throughput of Montgomery-type modular multiplication on one or more GPUs.
+
+Workload (one "step"): the 32-bit signed and Plantard-style variants on the
+moduli N = 3329 and N = 8380417, 2^26 operand pairs per modulus drawn
+uniformly from the centred range (-N/2, N/2] (the Plantard reduction gets the
+same residues lifted to [0, N)), R = 2^32 for the signed Montgomery reduction
+(Algorithm 1) and R = 2^64 for the Plantard reduction (Algorithm 2) and the
+two signed Plantard reductions (Algorithm 3; Algorithm 4 with alpha = 1).
+One step is 8 mont_mul launches of 2^26 elements: 5.4e8 modular products,
+6.4 GB of operand traffic.  Every operand array is 256 MiB, larger than the
+129 MB L2, so no flush is needed between steps.
+
+Output: one JSON line (rank 0).  ``value`` is Gmodmul/s with the operands
+resident in HBM; ``e2e`` is the same metric through the same C-ABI calls
+with the operands copied from pinned host memory and the products copied
+back inside the timed region.  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as sy  # noqa: E402
+
+METRIC = "Gmodmul/s"
+WORKLOAD = ("word32 mont_mul: Alg.1 SigRedc R=2^32, Alg.2 PRedc, Alg.3 SigPRedc1, "
+            "Alg.4 SigPRedc2(alpha=1) R=2^64; N in {3329, 8380417}; 2^26 pairs per modulus")
+N_PAIRS = 1 << 26
+MODULI = sy.WORD32_MODULI
+# (variant, log2R): Algorithm 1, 2, 3, 4
+COMBOS = ((1, 32), (2, 64), (3, 64), (4, 64))
+VARIANT_NAMES = {1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
+BYTES_PER_MODMUL = 12          # two 4-byte operands in, one 4-byte product out
+ALPHA = 1
+
+# DRAM bytes per launch of the word kernel on this workload, from one ncu
+# capture of the same launch (profiles/word32_mont_mul_2p26.md); None until
+# a capture of the current kernel exists.
+NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--e2e-steps", type=int, default=0, help="0: min(steps, 10)")
+    p.add_argument("--cpu-budget-s", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--log2-pairs", type=int, default=26,
+                   help="pairs per modulus = 2^this (26 is the benchmark workload)")
+    a = p.parse_args()
+    global N_PAIRS
+    N_PAIRS = 1 << a.log2_pairs
+    return a
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_inputs():
+    """Seeded operands per modulus: centred int32 and their [0, N) lift."""
+    out = {}
+    for N in MODULI:
+        a = sy.centred_residues(N, N_PAIRS, seed=2 * N + 1)
+        b = sy.centred_residues(N, N_PAIRS, seed=2 * N + 2)
+        out[N] = (a, b, sy.lift_unsigned(a, N), sy.lift_unsigned(b, N))
+    return out
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.25)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        # samples under load: the top of the distribution (idle gaps read low)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- cpu oracle
+
+def oracle_sample_rate(inputs, budget_s: float):
+    """Time the oracle (as it stands) on the first pairs of each of the 8
+    vectors until about budget_s seconds of CPU work; returns (Gmodmul/s,
+    pairs per vector, seconds)."""
+    import oracle as o
+    per = 64
+    done = 0
+    t_used = 0.0
+    while True:
+        t0 = time.perf_counter()
+        for N in MODULI:
+            a, b, au, bu = inputs[N]
+            for variant, l in COMBOS:
+                x, y = (au, bu) if variant == 2 else (a, b)
+                for i in range(done, done + per):
+                    o.mul_value(variant, int(x[i]), int(y[i]), N, l, ALPHA)
+        t_used += time.perf_counter() - t0
+        done += per
+        if t_used >= budget_s or done + 2 * per > N_PAIRS:
+            break
+        per *= 2
+    total = done * len(MODULI) * len(COMBOS)
+    return total / t_used / 1e9, done, t_used
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2402_00675_gb300 as mg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mg.build()
+    L = mg.lib()
+
+    inputs = make_inputs()
+    dev_in = {}
+    for N in MODULI:
+        dev_in[N] = tuple(torch.from_numpy(x).cuda() for x in inputs[N])
+    ctxs, outs, calls = {}, {}, []
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    for N in MODULI:
+        da, db, dau, dbu = dev_in[N]
+        for variant, l in COMBOS:
+            ctx = mg.mont_ctx_create(N, l, variant, alpha=ALPHA)
+            ctxs[(N, variant)] = ctx
+            out = torch.empty(N_PAIRS, dtype=torch.uint32 if variant == 2 else torch.int32,
+                              device="cuda")
+            outs[(N, variant)] = out
+            x, y = (dau, dbu) if variant == 2 else (da, db)
+            calls.append(((N, variant), ctx.handle, x.data_ptr(), y.data_ptr(), out.data_ptr()))
+
+    def step(evs=None, k=0):
+        for j, (_, h, xp, yp, op) in enumerate(calls):
+            if evs is not None:
+                evs[k][j][0].record(stream)
+            st = L.mont_mul(h, xp, yp, op, N_PAIRS, sptr)
+            if st:
+                raise mg.MontError(st, "mont_mul")
+            if evs is not None:
+                evs[k][j][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in calls] for _ in range(K)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    for k in range(K):
+        step(evs, k)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    per_launch = [[evs[k][j][0].elapsed_time(evs[k][j][1]) for k in range(K)]
+                  for j in range(len(calls))]
+    all_launch_ms = [x for row in per_launch for x in row]
+    avg_launch_ms = sum(all_launch_ms) / len(all_launch_ms)
+    per_variant = {}
+    for j, ((N, variant), *_rest) in enumerate(calls):
+        ms = sum(per_launch[j]) / K
+        per_variant[f"{VARIANT_NAMES[variant]}_N{N}"] = round(N_PAIRS / (ms * 1e-3) / 1e9, 2)
+
+    modmuls_per_step = N_PAIRS * len(calls)
+    value = world * modmuls_per_step * K / (elapsed_ms * 1e-3) / 1e9
+
+    # ---------------- end to end: pinned host operands in, products out
+    e2e_steps = args.e2e_steps or min(K, 10)
+    host_in = {N: tuple(torch.from_numpy(x).pin_memory() for x in inputs[N]) for N in MODULI}
+    host_out = {key: torch.empty(N_PAIRS, dtype=outs[key].dtype).pin_memory() for key in outs}
+    h2d = sum(t.numel() * t.element_size() for N in MODULI for t in host_in[N])
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+
+    def e2e_step():
+        for N in MODULI:
+            for d, h in zip(dev_in[N], host_in[N]):
+                d.copy_(h, non_blocking=True)
+        step()
+        for key, h in host_out.items():
+            h.copy_(outs[key], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * modmuls_per_step * e2e_steps / (e2e_ms * 1e-3) / 1e9
+
+    # ---------------- roofline of the dominant kernel (the word kernel)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = BYTES_PER_MODMUL * N_PAIRS / (avg_launch_ms * 1e-3) / 1e9
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, per, secs = oracle_sample_rate(inputs, args.cpu_budget_s)
+            cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "sample": f"first {per} pairs of each of the 8 (modulus, variant) vectors, "
+                             f"{per * 8} oracle products in {secs:.1f} s, Python big-int, 1 thread"}
+        result = {
+            "metric": METRIC, "value": round(value, 3), "unit": METRIC, "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/i32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_modulus": N_PAIRS, "moduli": list(MODULI),
+                       "launches_per_step": len(calls), "parallelism": f"replicas x{world}",
+                       "l2": "no flush: every operand array is 256 MiB, larger than the 129 MB L2"},
+            "e2e": {"value": round(e2e_value, 3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": len(calls) * K,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH,
+                         "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
+                         "kernel": "word_kernel (mont_mul, 32-bit words)",
+                         "avg_launch_us": round(avg_launch_ms * 1e3, 2),
+                         "algorithmic_bytes_per_launch": BYTES_PER_MODMUL * N_PAIRS},
+            "per_variant_gmodmul_s": per_variant,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step evaluates a bounded
+    sample of the same workload (the first pairs of each of the 8 vectors)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle as o
+    inputs = make_inputs()
+    # size a step so that warmup + steps take about a minute in total
+    probe_rate, _, _ = oracle_sample_rate(inputs, 0.5)
+    per_step_s = 60.0 / max(1, args.steps + args.warmup)
+    per = max(1, int(per_step_s * probe_rate * 1e9 / 8))
+
+    def step():
+        for N in MODULI:
+            a, b, au, bu = inputs[N]
+            for variant, l in COMBOS:
+                x, y = (au, bu) if variant == 2 else (a, b)
+                for i in range(per):
+                    o.mul_value(variant, int(x[i]), int(y[i]), N, l, ALPHA)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    secs = time.perf_counter() - t0
+    value = args.steps * per * 8 / secs / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/i32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_modulus": N_PAIRS, "moduli": list(MODULI),
+                   "sample_pairs_per_vector_per_step": per},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"first {per} pairs of each of the 8 (modulus, variant) "
+                                   "vectors per step, Python big-int, 1 thread"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * montgb -- Montgomery-type modular multiplication on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library.  The arithmetic follows Xu, Jia and Yang, "Chinese
+ * Remainder Theorem Approach to Montgomery-Type Algorithms": REDC (Section 1,
+ * derived from Qin's identity in Section 2, Eqs. (1)-(4)), the signed
+ * Montgomery reduction (Algorithm 1), Plantard's reduction (Algorithm 2) and
+ * the two signed Plantard reductions (Algorithms 3 and 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status: MONT_OK (0) or one of the MONT_E*
+ *   codes below.  Nothing aborts, prints or throws.  On MONT_ECUDA the CUDA
+ *   error code of the failing runtime call is kept per thread and returned by
+ *   mont_last_cuda_error().
+ * - "device pointer" arguments are addresses in the current CUDA device's
+ *   global memory, allocated and owned by the caller; the library never frees
+ *   or retains them past the call.  "host pointer" arguments are ordinary
+ *   process memory, also owned by the caller.
+ * - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *   stream.  Calls that take a stream only enqueue work on it and return
+ *   without synchronising, unless their comment says otherwise; the caller
+ *   must keep every buffer alive until that work completes.
+ * - Element layout: all integers are little-endian.  A ctx of word width 32
+ *   works on uint32_t (REDC, Plantard) or int32_t (signed variants) elements,
+ *   width 64 on uint64_t / int64_t elements, and a multi-limb ctx of k limbs
+ *   on elements of k consecutive uint32_t limbs, least significant first,
+ *   element i occupying limbs [i*k, (i+1)*k).
+ * - Alignment: device pointers must be aligned to their element's word size
+ *   (4 bytes for 32-bit words and limbs, 8 for 64-bit words, 16 for the
+ *   128-bit T of mont_redc at width 64); otherwise MONT_EINVAL.  Buffers that
+ *   are also 32-byte aligned take the 256-bit vector path; others take a
+ *   scalar path with identical results.
+ * - Inputs out of the range a variant's algorithm requires are not checked on
+ *   the device; the result for them is whatever the algorithm's formula
+ *   yields in the word arithmetic described at each variant.
+ */
+#ifndef MONTGB_H
+#define MONTGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define MONT_OK        0
+#define MONT_EINVAL    1  /* bad argument, unsupported (variant, width), precondition on N violated */
+#define MONT_ENOMEM    2  /* a host or device allocation failed */
+#define MONT_ECUDA     3  /* a CUDA runtime call failed; see mont_last_cuda_error() */
+#define MONT_ETIMEOUT  4  /* a bounded wait (device work-queue or host event) gave up */
+#define MONT_EOVERFLOW 5  /* an output buffer was too small; counts stay exact */
+
+/* -------------------------------------------------------------- variants */
+/* REDC (Section 1): returns T R^{-1} mod N in [0, N); requires N < R, 0 <= T < RN. */
+#define MONT_REDC              0
+/* SigRedc (Algorithm 1): returns r = T R^{-1} (mod N), -N < r < N;
+ * requires 2N < R and -NR/2 < T < NR/2. */
+#define MONT_SIGNED            1
+/* PRedc (Algorithm 2), R = 2^{2n}: returns -T R^{-1} mod N in [0, N);
+ * requires N < 2^n/phi (phi the golden ratio) and 0 <= T <= N^2. */
+#define MONT_PLANTARD          2
+/* SigPRedc1 (Algorithm 3), R = 2^{2n}: returns -T R^{-1} mods N;
+ * requires N < 2^{n-1} and |T| <= 2^{2n-2}. */
+#define MONT_SIGNED_PLANTARD   3
+/* SigPRedc2 (Algorithm 4), R = 2^{2n}, parameter alpha: returns
+ * -T R^{-1} mods N for alpha >= 1; requires N < 2^{n-alpha-1} and
+ * |T| <= 2^{2 alpha} N^2.  Section 3.3 shows alpha = 0 is wrong (Example 3.1);
+ * a ctx with alpha = 0 is refused, and the sweep below can test it. */
+#define MONT_SIGNED_PLANTARD2  4
+
+/* Largest multi-limb width: 64 limbs of 32 bits (2048-bit moduli). */
+#define MONT_MAX_LIMBS 64
+
+typedef struct mont_ctx* mont_ctx_t;  /* opaque; owned by the library */
+
+/*
+ * mont_ctx_create -- per-modulus precomputation (the constants of Section 1
+ * and Theorem 2.1: N^{-1} mod R, N' = R - N^{-1}, R mod N, R^2 mod N).
+ *
+ *   out      host pointer; receives the new ctx (left untouched on error).
+ *   N_limbs  host pointer to n_limbs little-endian 32-bit limbs of the odd
+ *            modulus N >= 3.  Upper limbs may be zero.
+ *   n_limbs  1 -> 32-bit word kernels, 2 -> 64-bit word kernels,
+ *            8..MONT_MAX_LIMBS -> multi-limb kernels (REDC only).
+ *   log2R    R = 2^log2R.  Must be 32*n_limbs for MONT_REDC and MONT_SIGNED,
+ *            and 64*n_limbs (the paper's R = 2^{2n} with n the word size) for
+ *            the three Plantard variants.
+ *   variant  one of the MONT_* variant codes.
+ *   alpha    Algorithm 4's parameter (>= 1); ignored by other variants.
+ *
+ * Errors: MONT_EINVAL if N is even or < 3, if N violates the variant's
+ * condition on N listed above, if (variant, n_limbs, log2R) is not a
+ * supported combination, or if a pointer is NULL; MONT_ENOMEM.
+ * The ctx holds host memory only; it can be used from any thread and on any
+ * stream, concurrently, and is freed by mont_ctx_destroy.
+ */
+int mont_ctx_create(mont_ctx_t* out, const uint32_t* N_limbs, int n_limbs,
+                    int log2R, int variant, int alpha);
+
+/* Free a ctx.  NULL is accepted.  Work already enqueued that used the ctx is
+ * unaffected (kernels receive the constants by value). */
+int mont_ctx_destroy(mont_ctx_t ctx);
+
+/* Which precomputed constant mont_ctx_constant returns. */
+#define MONT_CONST_N          0  /* N                                              */
+#define MONT_CONST_NINV       1  /* N^{-1} mod R, in [1, R)                         */
+#define MONT_CONST_NPRIME     2  /* N' = R - N^{-1} (Section 1)                     */
+#define MONT_CONST_R_MOD_N    3  /* R mod N                                         */
+#define MONT_CONST_R2_MOD_N   4  /* R^2 mod N, in [0, N)                            */
+#define MONT_CONST_DOMAIN_R2  5  /* constant mont_to_domain multiplies by: R^2 mod N
+                                    for unsigned variants, (R^2 mod N) mods N for
+                                    signed ones (two's complement in the limbs)    */
+
+/*
+ * mont_ctx_constant -- copy one precomputed constant out of a ctx, as
+ * little-endian 32-bit limbs (log2R/32 limbs for NINV and NPRIME, n_limbs
+ * limbs for the others), into the host buffer `limbs` of `cap` limbs.
+ * *n_out receives the number of limbs written.  MONT_EOVERFLOW if cap is too
+ * small (nothing written); MONT_EINVAL on a bad `which` or NULL pointer.
+ */
+int mont_ctx_constant(mont_ctx_t ctx, int which, uint32_t* limbs, int cap, int* n_out);
+
+/*
+ * mont_ctx_query -- shape of a ctx: word width in bits (32, 64 or 32*k),
+ * number of limbs of one element, bytes per element, variant, log2R, alpha.
+ * Any output pointer may be NULL.
+ */
+int mont_ctx_query(mont_ctx_t ctx, int* width_bits, int* n_limbs, int* elem_bytes,
+                   int* variant, int* log2R, int* alpha);
+
+/*
+ * mont_mul -- out[i] = reduce(a[i] * b[i]) for i in [0, n): the Montgomery-
+ * type product a b R^{-1} (REDC, Algorithm 1) or -a b R^{-1} (Algorithms 2-4)
+ * in the variant's output range.  a, b, out: device pointers of n elements
+ * each (element type per the ctx); out may alias a or b exactly (in place),
+ * but must not partially overlap them.  Inputs must lie in the variant's
+ * output range (so that T = a b is in the algorithm's input domain):
+ * [0, N) for REDC, Plantard and multi-limb; (-N, N) for Algorithm 1;
+ * the mods-N range [-(N-1)/2, (N-1)/2] for Algorithms 3 and 4.
+ * n = 0 is a no-op.  Asynchronous on `stream`.
+ */
+int mont_mul(mont_ctx_t ctx, const void* a, const void* b, void* out, size_t n,
+             void* stream);
+
+/*
+ * mont_redc -- out[i] = reduce(T[i]) for a caller-supplied double-width T:
+ * int64/uint64 at width 32, 128-bit two's complement (16 bytes, low word
+ * first) at width 64, 2k limbs at k limbs.  T must lie in the algorithm's
+ * input domain (see the variant codes).  Device pointers; asynchronous.
+ */
+int mont_redc(mont_ctx_t ctx, const void* T, void* out, size_t n, void* stream);
+
+/*
+ * mont_to_domain -- out[i] = reduce(x[i] * MONT_CONST_DOMAIN_R2): the
+ * representation x R mod N of Section 1's map Phi for REDC and Algorithm 1,
+ * and -x R mod N for the Plantard variants (whose reductions return
+ * -T R^{-1}, so products stay closed).  x must lie in the variant's input
+ * range as for mont_mul.  Device pointers; asynchronous; out may alias x.
+ */
+int mont_to_domain(mont_ctx_t ctx, const void* x, void* out, size_t n, void* stream);
+
+/*
+ * mont_from_domain -- out[i] = canonical(reduce(y[i])): leaves the
+ * representation; the result is in [0, N) for unsigned variants and in
+ * [-(N-1)/2, (N-1)/2] for signed ones, so from(to(x)) = x.  Device pointers;
+ * asynchronous; out may alias y.
+ */
+int mont_from_domain(mont_ctx_t ctx, const void* y, void* out, size_t n, void* stream);
+
+/* ------------------------------------------------------------- utilities */
+/* Static description of a status code; never NULL. */
+const char* mont_strerror(int status);
+/* CUDA error code (cudaError_t as int) of the last MONT_ECUDA on this thread. */
+int mont_last_cuda_error(void);
+/* cudaStreamSynchronize(stream); MONT_ECUDA on failure. */
+int mont_sync(void* stream);
+/* Library version as major*10000 + minor*100 + patch. */
+int mont_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MONTGB_H */

@@ -1,0 +1,250 @@
+"""Python binding of montgb, the GB300 Montgomery-type modular arithmetic library.
+
+Argument marshalling only: every function forwards to the C ABI declared in
+``include/montgb.h`` (same names, same arguments) through ctypes.  Device
+buffers may be given as CUDA ``torch.Tensor`` objects or as raw integer
+addresses; streams as ``torch.cuda.Stream`` objects, raw ``cudaStream_t``
+integers, or ``None`` for torch's current stream.  Every non-zero status is
+raised as ``MontError``.
+
+The library must have been built (``paper_2402_00675_gb300.build.build()``);
+importing a function whose library is missing raises immediately -- there is
+no fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB_PATH, build  # noqa: F401
+
+MONT_OK = 0
+MONT_EINVAL = 1
+MONT_ENOMEM = 2
+MONT_ECUDA = 3
+MONT_ETIMEOUT = 4
+MONT_EOVERFLOW = 5
+
+MONT_REDC = 0
+MONT_SIGNED = 1
+MONT_PLANTARD = 2
+MONT_SIGNED_PLANTARD = 3
+MONT_SIGNED_PLANTARD2 = 4
+SIGNED_VARIANTS = (MONT_SIGNED, MONT_SIGNED_PLANTARD, MONT_SIGNED_PLANTARD2)
+PLANTARD_VARIANTS = (MONT_PLANTARD, MONT_SIGNED_PLANTARD, MONT_SIGNED_PLANTARD2)
+MONT_MAX_LIMBS = 64
+
+MONT_CONST_N = 0
+MONT_CONST_NINV = 1
+MONT_CONST_NPRIME = 2
+MONT_CONST_R_MOD_N = 3
+MONT_CONST_R2_MOD_N = 4
+MONT_CONST_DOMAIN_R2 = 5
+
+
+class MontError(RuntimeError):
+    """A non-zero status from the C ABI."""
+
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {mont_strerror(status)} (status {status})"
+        if status == MONT_ECUDA:
+            msg += f", cudaError {mont_last_cuda_error()}"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded shared library (loads it on first use; raises if absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"montgb library not built ({LIB_PATH} missing): run "
+                "paper_2402_00675_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+_c = ctypes
+_vp = _c.c_void_p
+_sz = _c.c_size_t
+_int = _c.c_int
+_u32p = _c.POINTER(_c.c_uint32)
+
+
+def _declare(L):
+    sig = {
+        "mont_ctx_create": (_int, [_c.POINTER(_vp), _u32p, _int, _int, _int, _int]),
+        "mont_ctx_destroy": (_int, [_vp]),
+        "mont_ctx_constant": (_int, [_vp, _int, _u32p, _int, _c.POINTER(_int)]),
+        "mont_ctx_query": (_int, [_vp] + [_c.POINTER(_int)] * 6),
+        "mont_mul": (_int, [_vp, _vp, _vp, _vp, _sz, _vp]),
+        "mont_redc": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_to_domain": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_from_domain": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_strerror": (_c.c_char_p, [_int]),
+        "mont_last_cuda_error": (_int, []),
+        "mont_sync": (_int, [_vp]),
+        "mont_version": (_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _check(status: int, where: str) -> None:
+    if status != MONT_OK:
+        raise MontError(status, where)
+
+
+def _ptr(x):
+    """Device address of a tensor (must be CUDA and contiguous) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor (device pointer argument)")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x).__name__}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _nbytes(x):
+    return x.numel() * x.element_size() if hasattr(x, "numel") else None
+
+
+def _limbs(x: int, k: int):
+    if x < 0 or x >> (32 * k):
+        raise ValueError("value does not fit in the limbs")
+    return (ctypes.c_uint32 * k)(*[(x >> (32 * i)) & 0xFFFFFFFF for i in range(k)])
+
+
+class Ctx:
+    """An owned ``mont_ctx_t`` handle with the parameters it was made from."""
+
+    def __init__(self, handle, N, log2R, variant, alpha, n_limbs):
+        self.handle = handle
+        self.N = N
+        self.log2R = log2R
+        self.variant = variant
+        self.alpha = alpha
+        self.n_limbs = n_limbs
+        self.width = 32 * n_limbs
+        self.elem_bytes = 4 * n_limbs
+
+    def close(self):
+        if self.handle:
+            lib().mont_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.handle:
+            raise ValueError("ctx already destroyed")
+        return self.handle
+
+
+def mont_ctx_create(N: int, log2R: int, variant: int, alpha: int = 0,
+                    n_limbs: int | None = None) -> Ctx:
+    """Precompute the constants of modulus N (see ``mont_ctx_create`` in montgb.h).
+
+    ``n_limbs`` defaults to 1 for log2R of 32 (REDC family) or 64 (Plantard
+    family), 2 for 64/128, and log2R/32 for multi-limb REDC."""
+    if n_limbs is None:
+        n_limbs = log2R // 64 if variant in PLANTARD_VARIANTS else log2R // 32
+        n_limbs = max(n_limbs, 1)
+    h = ctypes.c_void_p()
+    _check(lib().mont_ctx_create(ctypes.byref(h), _limbs(N, n_limbs), n_limbs, log2R,
+                                 variant, alpha), "mont_ctx_create")
+    return Ctx(h.value, N, log2R, variant, alpha, n_limbs)
+
+
+def mont_ctx_destroy(ctx: Ctx) -> None:
+    ctx.close()
+
+
+def mont_ctx_constant(ctx: Ctx, which: int) -> int:
+    buf = (ctypes.c_uint32 * (2 * MONT_MAX_LIMBS + 8))()
+    n = ctypes.c_int()
+    _check(lib().mont_ctx_constant(ctx, which, buf, len(buf), ctypes.byref(n)),
+           "mont_ctx_constant")
+    return sum(int(buf[i]) << (32 * i) for i in range(n.value))
+
+
+def mont_ctx_query(ctx: Ctx) -> dict:
+    vals = [ctypes.c_int() for _ in range(6)]
+    _check(lib().mont_ctx_query(ctx, *[ctypes.byref(v) for v in vals]), "mont_ctx_query")
+    keys = ("width_bits", "n_limbs", "elem_bytes", "variant", "log2R", "alpha")
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def _count(ctx: Ctx, out, n, scale=1):
+    if n is not None:
+        return int(n)
+    nb = _nbytes(out)
+    if nb is None:
+        raise ValueError("n is required when out is a raw pointer")
+    return nb // (ctx.elem_bytes * scale)
+
+
+def mont_mul(ctx: Ctx, a, b, out, n: int | None = None, stream=None) -> None:
+    """out[i] = a[i] b[i] R^{-1} (or -a b R^{-1} for the Plantard family), on the device."""
+    _check(lib().mont_mul(ctx, _ptr(a), _ptr(b), _ptr(out), _count(ctx, out, n),
+                          _stream(stream)), "mont_mul")
+
+
+def mont_redc(ctx: Ctx, T, out, n: int | None = None, stream=None) -> None:
+    """out[i] = reduce(T[i]) for double-width T, on the device."""
+    _check(lib().mont_redc(ctx, _ptr(T), _ptr(out), _count(ctx, out, n), _stream(stream)),
+           "mont_redc")
+
+
+def mont_to_domain(ctx: Ctx, x, out, n: int | None = None, stream=None) -> None:
+    _check(lib().mont_to_domain(ctx, _ptr(x), _ptr(out), _count(ctx, out, n), _stream(stream)),
+           "mont_to_domain")
+
+
+def mont_from_domain(ctx: Ctx, y, out, n: int | None = None, stream=None) -> None:
+    _check(lib().mont_from_domain(ctx, _ptr(y), _ptr(out), _count(ctx, out, n),
+                                  _stream(stream)), "mont_from_domain")
+
+
+def mont_sync(stream=None) -> None:
+    _check(lib().mont_sync(_stream(stream)), "mont_sync")
+
+
+def mont_strerror(status: int) -> str:
+    return lib().mont_strerror(status).decode()
+
+
+def mont_last_cuda_error() -> int:
+    return lib().mont_last_cuda_error()
+
+
+def mont_version() -> int:
+    return lib().mont_version()

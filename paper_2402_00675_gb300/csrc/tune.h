@@ -1,0 +1,20 @@
+// Launch-shape selection for the element-wise kernels.
+#pragma once
+
+#include "internal.h"
+
+namespace montgb {
+
+// Shape the element-wise launcher uses for (word width, variant, mode):
+// the autotuner's choice for the current device when one is recorded,
+// otherwise the built-in default.
+LaunchShape tuned_shape(int width, int variant, int mode);
+
+// Record a shape for the current device (used by the autotuner).
+void set_tuned_shape(int width, int variant, int mode, const LaunchShape& shape);
+
+// Multi-limb element-wise operations (cios.cu).
+int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y, void* out,
+                        size_t n, void* stream);
+
+}  // namespace montgb

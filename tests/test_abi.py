@@ -1,0 +1,160 @@
+"""The C-ABI library: it builds, loads, exports every declared symbol, and its
+host-side precomputation (the per-modulus constants) matches the oracle.
+No test here launches a kernel; all run without a GPU."""
+
+import ctypes
+import glob
+import os
+import random
+import re
+
+import pytest
+
+import oracle as o
+import paper_2402_00675_gb300 as mg
+from paper_2402_00675_gb300.build import build, INCLUDE
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return mg.lib()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(INCLUDE, "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        names += re.findall(r"\b(mont_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_version_and_strerror(L):
+    assert mg.mont_version() >= 10000
+    for s in range(0, 7):
+        assert isinstance(mg.mont_strerror(s), str) and mg.mont_strerror(s)
+
+
+def _const(ctx, which):
+    return mg.mont_ctx_constant(ctx, which)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("width", [32, 64])
+def test_host_precompute_matches_oracle(L, variant, width):
+    rnd = random.Random(100 * variant + width)
+    log2R = width if variant < 2 else 2 * width
+    n = width
+    moduli = [3, 5, 3329, 8380417]
+    while len(moduli) < 40:
+        N = rnd.randrange(3, 1 << width) | 1
+        moduli.append(N)
+    for N in moduli:
+        ok = o.precondition_ok(variant, N, log2R, 1)
+        if not ok:
+            with pytest.raises(mg.MontError) as ei:
+                mg.mont_ctx_create(N, log2R, variant, alpha=1)
+            assert ei.value.status == mg.MONT_EINVAL
+            continue
+        ctx = mg.mont_ctx_create(N, log2R, variant, alpha=1)
+        c = o.constants(N, log2R)
+        assert _const(ctx, mg.MONT_CONST_N) == N
+        assert _const(ctx, mg.MONT_CONST_NINV) == c.Ninv
+        assert _const(ctx, mg.MONT_CONST_NPRIME) == c.Nprime
+        assert _const(ctx, mg.MONT_CONST_R_MOD_N) == c.R_mod_N
+        assert _const(ctx, mg.MONT_CONST_R2_MOD_N) == c.R2_mod_N
+        dr2 = _const(ctx, mg.MONT_CONST_DOMAIN_R2)
+        if variant in (1, 3, 4):
+            want = o.mods(c.R2_mod_N, N) % (1 << width)  # two's complement word
+        else:
+            want = c.R2_mod_N
+        assert dr2 == want
+        q = mg.mont_ctx_query(ctx)
+        assert q["width_bits"] == width and q["log2R"] == log2R and q["variant"] == variant
+
+
+@pytest.mark.parametrize("k", [4, 8, 12, 16, 32, 64])
+def test_multilimb_precompute_matches_oracle(L, k):
+    rnd = random.Random(k)
+    for _ in range(5):
+        N = rnd.randrange(1 << (32 * k - 1), 1 << (32 * k)) | 1
+        ctx = mg.mont_ctx_create(N, 32 * k, 0)
+        c = o.constants(N, 32 * k)
+        assert _const(ctx, mg.MONT_CONST_NPRIME) == c.Nprime
+        assert _const(ctx, mg.MONT_CONST_R2_MOD_N) == c.R2_mod_N
+        assert _const(ctx, mg.MONT_CONST_R_MOD_N) == c.R_mod_N
+    # a modulus with leading zero limbs is accepted too
+    N = (1 << 100) + 3
+    ctx = mg.mont_ctx_create(N, 32 * 8, 0, n_limbs=8)
+    assert _const(ctx, mg.MONT_CONST_R2_MOD_N) == o.constants(N, 256).R2_mod_N
+
+
+def test_precondition_boundaries(L):
+    # Plantard, n = 32: N < 2^32/phi = 2654435769.49...
+    assert o.plantard_bound_ok(2654435769, 32) and not o.plantard_bound_ok(2654435771, 32)
+    mg.mont_ctx_create(2654435769, 64, mg.MONT_PLANTARD)
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create(2654435771, 64, mg.MONT_PLANTARD)
+    # Algorithm 1: 2N < R
+    mg.mont_ctx_create((1 << 31) - 1, 32, mg.MONT_SIGNED)
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create((1 << 31) + 1, 32, mg.MONT_SIGNED)
+    # Algorithm 3: N < 2^{n-1}
+    mg.mont_ctx_create((1 << 31) - 1, 64, mg.MONT_SIGNED_PLANTARD)
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create((1 << 31) + 1, 64, mg.MONT_SIGNED_PLANTARD)
+    # Algorithm 4: alpha >= 1 and N < 2^{n-alpha-1}
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create(3329, 64, mg.MONT_SIGNED_PLANTARD2, alpha=0)
+    mg.mont_ctx_create((1 << 30) - 1, 64, mg.MONT_SIGNED_PLANTARD2, alpha=1)
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create((1 << 30) + 1, 64, mg.MONT_SIGNED_PLANTARD2, alpha=1)
+    # even and tiny moduli, wrong log2R, Plantard on multi-limb
+    for bad in ((3328, 32, 0), (1, 32, 0), (3329, 32, 2)):
+        with pytest.raises(mg.MontError):
+            mg.mont_ctx_create(*bad)
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create(3329, 64, 0, n_limbs=1)          # log2R must be 32 n_limbs
+    with pytest.raises(mg.MontError):
+        mg.mont_ctx_create((1 << 255) + 1, 512, mg.MONT_PLANTARD, n_limbs=8)
+    # REDC accepts N up to R - 1
+    mg.mont_ctx_create((1 << 32) - 1, 32, 0)
+    mg.mont_ctx_create((1 << 64) - 59, 64, 0)
+
+
+def test_argument_errors_need_no_gpu(L):
+    ctx = mg.mont_ctx_create(3329, 32, 0)
+    # n = 0 is a no-op; NULL ctx and NULL pointers are refused before any launch
+    assert L.mont_mul(ctx.handle, None, None, None, 0, None) == mg.MONT_OK
+    assert L.mont_mul(None, 16, 16, 16, 4, None) == mg.MONT_EINVAL
+    assert L.mont_mul(ctx.handle, None, 16, 16, 4, None) == mg.MONT_EINVAL
+    # misaligned element pointers and partial overlap
+    assert L.mont_mul(ctx.handle, 4096 + 1, 8192, 12288, 4, None) == mg.MONT_EINVAL
+    assert L.mont_mul(ctx.handle, 4096, 8192, 4096 + 4, 4, None) == mg.MONT_EINVAL
+    assert L.mont_redc(ctx.handle, 4096 + 4, 8192, 4, None) == mg.MONT_EINVAL
+    buf = (ctypes.c_uint32 * 1)()
+    n = ctypes.c_int()
+    assert L.mont_ctx_constant(ctx.handle, mg.MONT_CONST_R2_MOD_N, buf, 0, ctypes.byref(n)) == \
+        mg.MONT_EOVERFLOW
+    assert L.mont_ctx_constant(ctx.handle, 99, buf, 1, ctypes.byref(n)) == mg.MONT_EINVAL
+    assert L.mont_ctx_destroy(None) == mg.MONT_OK
+
+
+def test_product_path_has_no_fallback(monkeypatch, tmp_path):
+    """With the library missing the binding raises instead of computing."""
+    import importlib
+    monkeypatch.setattr(mg, "_lib", None)
+    monkeypatch.setattr(mg, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        mg.lib()

@@ -1,0 +1,203 @@
+"""GPU parity of the 32- and 64-bit word kernels against the oracle.
+
+Every comparison is exact (integer results, bit for bit).  Sizes span many
+vectors and blocks plus a ragged tail; edge cases cover n in {1, 3, ...}
+(shorter than one vector), misaligned buffers (scalar and 128-bit paths),
+in-place operation, the extreme operands 0, 1, N-1 and the largest modulus
+each variant admits."""
+
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+import paper_2402_00675_gb300 as mg
+from gpu_helpers import (dev, dev_wide, empty_like_elems, host, input_range, log2R_of,
+                         max_modulus, np_dtype, sync)
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [0, 1, 2, 3, 4]
+WIDTHS = [32, 64]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mg.build()
+    assert torch.cuda.is_available()
+
+
+def moduli_for(variant, width, rnd):
+    l = log2R_of(variant, width)
+    top = max_modulus(variant, width)
+    out = [3, 3329, top]
+    if width == 32:
+        out.append(8380417 if o.precondition_ok(variant, 8380417, l, 1) else 12289)
+    while len(out) < 6:
+        N = rnd.randrange(3, top + 1) | 1
+        if o.precondition_ok(variant, N, l, 1):
+            out.append(N)
+    return out
+
+
+def operands(variant, N, n, rnd):
+    lo, hi = input_range(variant, N)
+    edges = [lo, hi, 0, 1 if hi >= 1 else 0, hi - 1 if hi > lo else hi]
+    xs = [rnd.randint(lo, hi) for _ in range(n)]
+    for i, e in enumerate(edges[: min(len(edges), n)]):
+        xs[i] = e
+    return xs
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_mul_parity(variant, width):
+    rnd = random.Random(1000 * variant + width)
+    l = log2R_of(variant, width)
+    dt = np_dtype(variant, width)
+    for idx, N in enumerate(moduli_for(variant, width, rnd)):
+        n = 100_003 if idx == 1 else 4099
+        ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
+        a = operands(variant, N, n, rnd)
+        b = operands(variant, N, n, rnd)
+        b[:5] = list(reversed(b[:5]))
+        out = empty_like_elems(n, dt)
+        mg.mont_mul(ctx, dev(a, dt), dev(b, dt), out)
+        sync()
+        got = host(out)
+        want = [o.mul_value(variant, x, y, N, l, 1) for x, y in zip(a, b)]
+        assert got == want, (variant, width, N)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_domain_maps_parity(variant, width):
+    rnd = random.Random(2000 * variant + width)
+    l = log2R_of(variant, width)
+    dt = np_dtype(variant, width)
+    for N in moduli_for(variant, width, rnd)[:4]:
+        ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
+        n = 5003
+        x = operands(variant, N, n, rnd)
+        if variant in (3, 4):
+            pass
+        elif variant == 1:
+            x = [o.mods(v, N) for v in x]     # canonical inputs for the round trip
+        y = empty_like_elems(n, dt)
+        mg.mont_to_domain(ctx, dev(x, dt), y)
+        back = empty_like_elems(n, dt)
+        mg.mont_from_domain(ctx, y, back)
+        sync()
+        gy = host(y)
+        assert gy == [o.to_domain_value(variant, v, N, l, 1) for v in x]
+        assert host(back) == [o.from_domain_value(variant, v, N, l, 1) for v in gy]
+        assert host(back) == x
+        # from_domain on arbitrary outputs of the variant's range
+        z = operands(variant, N, n, rnd)
+        zo = empty_like_elems(n, dt)
+        mg.mont_from_domain(ctx, dev(z, dt), zo)
+        sync()
+        assert host(zo) == [o.from_domain_value(variant, v, N, l, 1) for v in z]
+
+
+def redc_inputs(variant, N, l, n, rnd, alpha=1):
+    lo, hi = o.input_domain(variant, N, l, alpha)
+    T = [rnd.randint(lo, hi) for _ in range(n)]
+    edges = [lo, hi, 0, lo + 1, hi - 1]
+    T[: len(edges)] = edges
+    return T
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_redc_parity(variant, width):
+    rnd = random.Random(3000 * variant + width)
+    l = log2R_of(variant, width)
+    dt = np_dtype(variant, width)
+    for N in moduli_for(variant, width, rnd):
+        ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
+        n = 6007
+        T = redc_inputs(variant, N, l, n, rnd)
+        out = empty_like_elems(n, dt)
+        mg.mont_redc(ctx, dev_wide(T, width), out)
+        sync()
+        assert host(out) == [o.reduce_value(variant, t, N, l, 1) for t in T], (variant, N)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ragged_sizes_alignment_and_in_place(variant, width):
+    rnd = random.Random(4000 * variant + width)
+    l = log2R_of(variant, width)
+    dt = np_dtype(variant, width)
+    N = moduli_for(variant, width, rnd)[2]
+    ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
+    for n in (1, 2, 3, 5, 7, 8, 9, 15, 16, 17, 31, 33, 63, 65, 257, 1023, 2049):
+        for pad in (0, 1, 2, 4):
+            a = operands(variant, N, n, rnd)
+            b = operands(variant, N, n, rnd)
+            want = [o.mul_value(variant, x, y, N, l, 1) for x, y in zip(a, b)]
+            da, db = dev(a, dt, pad), dev(b, dt, pad)
+            out = empty_like_elems(n, dt, pad)
+            mg.mont_mul(ctx, da, db, out)
+            sync()
+            assert host(out) == want, (n, pad)
+            mg.mont_mul(ctx, da, db, da)          # in place over a
+            sync()
+            assert host(da) == want, (n, pad, "in place")
+    # n = 0 touches nothing
+    z = empty_like_elems(4, dt)
+    mg.mont_mul(ctx, z, z, z, n=0)
+    sync()
+
+
+def test_full_size_redc32_2p20():
+    """REDC, R = 2^32, N = 3329, 2^20 pairs uniform in [0, N): sampled parity
+    plus the range property on every element."""
+    import synthetic as sy
+    N, n = sy.REDC32_N, 1 << 20
+    a = sy.uniform_residues(N, n, seed=1)
+    b = sy.uniform_residues(N, n, seed=101)
+    ctx = mg.mont_ctx_create(N, 32, 0)
+    out = torch.empty(n, dtype=torch.uint32, device="cuda")
+    mg.mont_mul(ctx, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), out)
+    sync()
+    got = out.cpu().numpy()
+    assert int(got.max()) < N
+    rnd = random.Random(5)
+    idx = list(range(2000)) + list(range(n - 2000, n)) + [rnd.randrange(n) for _ in range(20000)]
+    for i in idx:
+        assert int(got[i]) == o.mul_value(0, int(a[i]), int(b[i]), N, 32), i
+
+
+@pytest.mark.parametrize("N", [3329, 8380417])
+def test_full_size_word32_variants_2p26(N):
+    """The 2^26-pair workload of the signed and Plantard variants, as the
+    benchmark launches it: sampled element parity plus the claimed range of
+    every element."""
+    import synthetic as sy
+    n = 1 << 26
+    a = sy.centred_residues(N, n, seed=2 * N + 1)
+    b = sy.centred_residues(N, n, seed=2 * N + 2)
+    au, bu = sy.lift_unsigned(a, N), sy.lift_unsigned(b, N)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    dau, dbu = torch.from_numpy(au).cuda(), torch.from_numpy(bu).cuda()
+    rnd = random.Random(N)
+    idx = list(range(1000)) + list(range(n - 1000, n)) + [rnd.randrange(n) for _ in range(8000)]
+    for variant, l in ((1, 32), (2, 64), (3, 64), (4, 64)):
+        ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
+        signed = variant != 2
+        out = torch.empty(n, dtype=torch.int32 if signed else torch.uint32, device="cuda")
+        if signed:
+            mg.mont_mul(ctx, da, db, out)
+        else:
+            mg.mont_mul(ctx, dau, dbu, out)
+        sync()
+        got = out.cpu().numpy().astype(np.int64)
+        lo, hi = o.claimed_range(variant, N)
+        assert got.min() >= lo and got.max() <= hi
+        xa, xb = (a, b) if signed else (au, bu)
+        for i in idx:
+            assert int(got[i]) == o.mul_value(variant, int(xa[i]), int(xb[i]), N, l, 1), (variant, i)
