@@ -170,6 +170,130 @@ int mont_to_domain(mont_ctx_t ctx, const void* x, void* out, size_t n, void* str
  */
 int mont_from_domain(mont_ctx_t ctx, const void* y, void* out, size_t n, void* stream);
 
+/* ---------------------------------------------------------- batched RNS */
+/*
+ * mont_mul_batched -- many independent mont_mul problems in one persistent
+ * launch: for each j in [0, count), out[j][i] = reduce(a[j][i] * b[j][i]) for
+ * i in [0, lens[j]) with the modulus, variant and constants of ctxs[j]
+ * (Section 1 / Algorithms 1-4, as mont_mul).  This is the residue-number-system
+ * pattern: one vector per modulus, lengths as uneven as the caller likes.
+ *
+ *   ctxs, a, b, out, lens  host arrays of `count` entries; a[j], b[j], out[j]
+ *          are device pointers with mont_mul's rules (element alignment, in
+ *          place allowed, no partial overlap).  lens[j] = 0 is allowed (the
+ *          pointers of that entry are then ignored).
+ *   Every ctx must have the same word width, 32 or 64 (multi-limb contexts
+ *   are refused); variants may differ.  Asynchronous on `stream`.  Vectors of
+ *   up to 128 moduli go into one launch; larger batches take one launch per
+ *   128.  No device memory is allocated: the per-modulus constants travel in
+ *   the launch's parameters and are staged in shared memory.
+ * Errors: MONT_EINVAL on mixed widths, NULL or misaligned pointers.
+ */
+int mont_mul_batched(const mont_ctx_t* ctxs, const void* const* a, const void* const* b,
+                     void* const* out, const size_t* lens, int count, void* stream);
+
+/*
+ * A batch plan: the launches of mont_mul_batched for one fixed set of
+ * (ctx, length) pairs, recorded once in a CUDA graph and replayed with a single
+ * graph launch.  The plan copies everything it needs; ctxs may be destroyed
+ * after mont_batch_create returns.
+ *
+ * mont_batch_create  -- same arguments and rules as mont_mul_batched (host
+ *                       arrays; device operand pointers); builds and
+ *                       instantiates the graph on the current device.
+ * mont_batch_launch  -- enqueue the graph on `stream` (asynchronous).  A plan
+ *                       must not be launched concurrently with itself
+ *                       while its pointers are being updated.
+ * mont_batch_update  -- replace the operand pointers (host arrays of `count`
+ *                       device pointers; entries with length 0 are ignored);
+ *                       shapes stay fixed.  Affects later launches only.
+ * mont_batch_destroy -- free the plan (NULL accepted); launches already
+ *                       enqueued complete normally.
+ */
+typedef struct mont_batch* mont_batch_t;
+int mont_batch_create(mont_batch_t* out_batch, const mont_ctx_t* ctxs, const void* const* a,
+                      const void* const* b, void* const* out, const size_t* lens, int count);
+int mont_batch_launch(mont_batch_t batch, void* stream);
+int mont_batch_update(mont_batch_t batch, const void* const* a, const void* const* b,
+                      void* const* out);
+int mont_batch_destroy(mont_batch_t batch);
+
+/* ------------------------------------------------------- verify sweep */
+/*
+ * The exhaustive check of Section 3: for every odd N in [N_lo, N_hi] and every T
+ * of a domain, evaluate the variant's algorithm (REDC of Section 1, Algorithms
+ * 1-4) exactly as written, at R = 2^log2R, and count T whose output r is a
+ * counterexample to the claim derived from Eq. (5):
+ *     r != s T R^{-1} (mod N)   or   r outside the claimed range,
+ * with s = +1 for REDC and Algorithm 1, s = -1 for the Plantard family.
+ * Example 3.1 is such a counterexample of Algorithm 4 with alpha = 0.
+ */
+#define MONT_DOMAIN_DEFAULT   0  /* the algorithm's own Require line (inclusive bounds)        */
+#define MONT_DOMAIN_REDC      1  /* 0 <= T < R N, Section 1's domain, for every variant        */
+#define MONT_DOMAIN_EXPLICIT  2  /* t_lo <= T <= t_hi for every N                             */
+#define MONT_RANGE_DEFAULT    0  /* the algorithm's own Ensure line                           */
+#define MONT_RANGE_UNSIGNED   1  /* 0 <= r <= N-1                                             */
+#define MONT_RANGE_WIDE       2  /* -(N-1) <= r <= N-1                                        */
+#define MONT_RANGE_CENTRED    3  /* -(N-1)/2 <= r <= (N-1)/2                                  */
+#define MONT_RANGE_EXPLICIT   4  /* r_lo <= r <= r_hi for every N                             */
+
+typedef struct mont_bounds {
+  int domain_rule;   /* MONT_DOMAIN_*                                  */
+  int range_rule;    /* MONT_RANGE_*                                   */
+  int64_t t_lo, t_hi; /* used by MONT_DOMAIN_EXPLICIT (inclusive)      */
+  int64_t r_lo, r_hi; /* used by MONT_RANGE_EXPLICIT (inclusive)       */
+} mont_bounds;
+
+typedef struct mont_cex {  /* one counterexample                        */
+  uint32_t N;
+  uint32_t reserved;
+  int64_t T;
+  int64_t r;         /* the algorithm's output                          */
+  int64_t expected;  /* the canonical target: s T R^{-1} mod N (REDC, Algorithm 2)
+                        or mods N (Algorithms 1, 3, 4)                   */
+} mont_cex;
+
+#define MONT_SWEEP_INCLUDE_OUT_OF_SPEC 1  /* also sweep N that violate the variant's
+                                             condition on N (skipped by default) */
+
+/* Limits of the sweep: 2 <= log2R <= 16 (even for the Plantard family);
+ * 3 <= N_lo <= N_hi < 2^15; every swept T and every claimed bound within
+ * [-2^31, 2^31 - 1]; 0 <= alpha <= 14.  These keep every intermediate of the
+ * algorithms inside a 32-bit register (64-bit for REDC's T + mN). */
+#define MONT_SWEEP_MAX_LOG2R 16
+#define MONT_SWEEP_MAX_N     32767
+
+/*
+ * mont_verify_sweep -- run the sweep on the device and return its results on
+ * the host.  Synchronous: returns after the results are copied back.
+ *
+ *   variant, log2R, alpha  the algorithm under test and its R = 2^log2R; alpha
+ *                  (Algorithm 4 only) may be 0 here, unlike in mont_ctx_create.
+ *   N_lo, N_hi     inclusive range; even values are skipped.
+ *   claimed        host pointer to the domain and range rules, or NULL for
+ *                  (MONT_DOMAIN_DEFAULT, MONT_RANGE_DEFAULT).
+ *   flags          0 or MONT_SWEEP_INCLUDE_OUT_OF_SPEC.
+ *   per_N_counts   host array of n_odd = number of odd N in [N_lo, N_hi]
+ *                  entries, entry i for the i-th odd N: the exact number of
+ *                  counterexamples (0 for skipped N).
+ *   per_N_checked  host array of n_odd entries receiving the number of T
+ *                  checked per N (0 for skipped N), or NULL.
+ *   cex, cex_cap   host array for up to cex_cap counterexamples, sorted by
+ *                  (N, T); may be NULL when cex_cap = 0.
+ *   n_cex_total    host pointer receiving the total number of counterexamples.
+ *   stream         the stream the sweep runs on (it is synchronised).
+ *
+ * Returns MONT_EOVERFLOW when n_cex_total > cex_cap: the counts are exact, and
+ * cex holds cex_cap of the counterexamples (which ones is unspecified), sorted.
+ * MONT_EINVAL outside the limits above; MONT_ENOMEM / MONT_ECUDA on device
+ * failures.  Device scratch (the counters and the example buffer) is allocated
+ * and freed on the stream by the call.
+ */
+int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t N_hi,
+                      const mont_bounds* claimed, int flags, uint64_t* per_N_counts,
+                      uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
+                      size_t* n_cex_total, void* stream);
+
 /* ------------------------------------------------------------- utilities */
 /* Static description of a status code; never NULL. */
 const char* mont_strerror(int status);

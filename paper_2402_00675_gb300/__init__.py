@@ -42,6 +42,29 @@ MONT_CONST_R_MOD_N = 3
 MONT_CONST_R2_MOD_N = 4
 MONT_CONST_DOMAIN_R2 = 5
 
+MONT_DOMAIN_DEFAULT = 0
+MONT_DOMAIN_REDC = 1
+MONT_DOMAIN_EXPLICIT = 2
+MONT_RANGE_DEFAULT = 0
+MONT_RANGE_UNSIGNED = 1
+MONT_RANGE_WIDE = 2
+MONT_RANGE_CENTRED = 3
+MONT_RANGE_EXPLICIT = 4
+MONT_SWEEP_INCLUDE_OUT_OF_SPEC = 1
+MONT_SWEEP_MAX_LOG2R = 16
+MONT_SWEEP_MAX_N = 32767
+
+
+class MontBounds(ctypes.Structure):
+    _fields_ = [("domain_rule", ctypes.c_int), ("range_rule", ctypes.c_int),
+                ("t_lo", ctypes.c_int64), ("t_hi", ctypes.c_int64),
+                ("r_lo", ctypes.c_int64), ("r_hi", ctypes.c_int64)]
+
+
+class MontCex(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("T", ctypes.c_int64),
+                ("r", ctypes.c_int64), ("expected", ctypes.c_int64)]
+
 
 class MontError(RuntimeError):
     """A non-zero status from the C ABI."""
@@ -88,6 +111,17 @@ def _declare(L):
         "mont_redc": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_to_domain": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_from_domain": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_verify_sweep": (_int, [_int, _int, _int, _c.c_uint32, _c.c_uint32,
+                                     _c.POINTER(MontBounds), _int,
+                                     _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64),
+                                     _c.POINTER(MontCex), _sz, _c.POINTER(_sz), _vp]),
+        "mont_mul_batched": (_int, [_c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp),
+                                    _c.POINTER(_vp), _c.POINTER(_sz), _int, _vp]),
+        "mont_batch_create": (_int, [_c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp),
+                                     _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_sz), _int]),
+        "mont_batch_launch": (_int, [_vp, _vp]),
+        "mont_batch_update": (_int, [_vp, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
+        "mont_batch_destroy": (_int, [_vp]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -232,6 +266,108 @@ def mont_to_domain(ctx: Ctx, x, out, n: int | None = None, stream=None) -> None:
 def mont_from_domain(ctx: Ctx, y, out, n: int | None = None, stream=None) -> None:
     _check(lib().mont_from_domain(ctx, _ptr(y), _ptr(out), _count(ctx, out, n),
                                   _stream(stream)), "mont_from_domain")
+
+
+def _batch_arrays(ctxs, a, b, out, lens):
+    count = len(ctxs)
+    if not (len(a) == len(b) == len(out) == count):
+        raise ValueError("ctxs, a, b, out must have the same length")
+    if lens is None:
+        lens = [_count(c, o, None) for c, o in zip(ctxs, out)]
+    P = ctypes.c_void_p * max(count, 1)
+    return (count, P(*[c.handle for c in ctxs]), P(*[_ptr(x) for x in a]),
+            P(*[_ptr(x) for x in b]), P(*[_ptr(x) for x in out]),
+            (ctypes.c_size_t * max(count, 1))(*[int(n) for n in lens]))
+
+
+def mont_mul_batched(ctxs, a, b, out, lens=None, stream=None) -> None:
+    """One persistent launch over many (modulus, vector) pairs; see montgb.h."""
+    count, C, A, B, O, Ls = _batch_arrays(ctxs, a, b, out, lens)
+    _check(lib().mont_mul_batched(C, A, B, O, Ls, count, _stream(stream)), "mont_mul_batched")
+
+
+class Batch:
+    """A mont_batch_t plan: the batch's launches recorded in a CUDA graph."""
+
+    def __init__(self, ctxs, a, b, out, lens=None):
+        count, C, A, B, O, Ls = _batch_arrays(ctxs, a, b, out, lens)
+        h = ctypes.c_void_p()
+        _check(lib().mont_batch_create(ctypes.byref(h), C, A, B, O, Ls, count),
+               "mont_batch_create")
+        self.handle = h.value
+        self.count = count
+
+    def launch(self, stream=None) -> None:
+        _check(lib().mont_batch_launch(self.handle, _stream(stream)), "mont_batch_launch")
+
+    def update(self, a, b, out) -> None:
+        P = ctypes.c_void_p * max(self.count, 1)
+        _check(lib().mont_batch_update(self.handle, P(*[_ptr(x) for x in a]),
+                                       P(*[_ptr(x) for x in b]), P(*[_ptr(x) for x in out])),
+               "mont_batch_update")
+
+    def close(self):
+        if self.handle:
+            lib().mont_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mont_batch_create(ctxs, a, b, out, lens=None) -> Batch:
+    return Batch(ctxs, a, b, out, lens)
+
+
+def mont_batch_launch(batch: Batch, stream=None) -> None:
+    batch.launch(stream)
+
+
+def mont_batch_update(batch: Batch, a, b, out) -> None:
+    batch.update(a, b, out)
+
+
+def mont_batch_destroy(batch: Batch) -> None:
+    batch.close()
+
+
+class SweepResult:
+    """Host-side result of mont_verify_sweep."""
+
+    def __init__(self, moduli, counts, checked, examples, total, overflow):
+        self.moduli = moduli            # the odd N of the range, in order
+        self.counts = counts            # N -> counterexamples (0 for skipped N)
+        self.checked = checked          # N -> T checked (0 for skipped N)
+        self.examples = examples        # sorted (N, T, r, expected)
+        self.total = total
+        self.overflow = overflow        # more counterexamples than cex_cap
+
+
+def mont_verify_sweep(variant: int, log2R: int, alpha: int, N_lo: int, N_hi: int,
+                      claimed: MontBounds | None = None, flags: int = 0,
+                      cex_cap: int = 1 << 16, stream=None) -> SweepResult:
+    """Run the exhaustive sweep on the device (synchronous); see montgb.h."""
+    first = N_lo if N_lo % 2 else N_lo + 1
+    moduli = list(range(first, N_hi + 1, 2))
+    n = max(len(moduli), 1)
+    counts = (ctypes.c_uint64 * n)()
+    checked = (ctypes.c_uint64 * n)()
+    cex = (MontCex * max(cex_cap, 1))()
+    total = ctypes.c_size_t()
+    st = lib().mont_verify_sweep(variant, log2R, alpha, N_lo, N_hi,
+                                 ctypes.byref(claimed) if claimed is not None else None, flags,
+                                 counts, checked, cex, cex_cap, ctypes.byref(total),
+                                 _stream(stream))
+    if st not in (MONT_OK, MONT_EOVERFLOW):
+        raise MontError(st, "mont_verify_sweep")
+    nrec = min(total.value, cex_cap)
+    ex = [(int(c.N), int(c.T), int(c.r), int(c.expected)) for c in cex[:nrec]]
+    return SweepResult(moduli, {N: int(counts[i]) for i, N in enumerate(moduli)},
+                       {N: int(checked[i]) for i, N in enumerate(moduli)}, ex, total.value,
+                       st == MONT_EOVERFLOW)
 
 
 def mont_sync(stream=None) -> None:

@@ -52,6 +52,7 @@ struct LaunchShape {
   int unroll = 2;           // vectors in flight per thread per operand
   int vec_bytes = 32;       // 32 (256-bit), 16 (128-bit) or 0 (scalar path)
   int blocks_per_sm = 0;    // 0: as many as the occupancy calculator allows
+  int tile_iters = 2;       // batched kernel: CTA iterations per tile
 };
 
 enum class Mode : int { kMul = 0, kToDomain = 1, kFromDomain = 2, kRedc = 3 };
@@ -66,6 +67,10 @@ cudaError_t launch_word64(int variant, Mode mode, const WordConst64& c, const vo
 
 // Number of SMs of the current device (cached per device).
 int device_sm_count();
+
+// Occupancy-derived resident blocks per SM of a kernel at a block size
+// (cached per kernel, block size and device).
+int resident_blocks(const void* kernel, int threads);
 
 }  // namespace montgb
 

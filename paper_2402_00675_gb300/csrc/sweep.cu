@@ -1,0 +1,357 @@
+// Exhaustive verify sweep (mont_verify_sweep): the CRT check of Section 3.
+//
+// Work decomposition.  The host lists the swept moduli in a table (one entry
+// per odd N with its constants, its T interval and its claimed output range)
+// and cuts each N's T interval into chunks of C consecutive T; chunk i of the
+// whole sweep belongs to the entry whose first chunk index is the largest one
+// <= i.  A grid of resident threads walks the chunk indices grid-stride.
+//
+// Per chunk, a thread evaluates the algorithm on every T exactly as the paper
+// writes it (REDC of Section 1, Algorithms 1-4), in 32/64-bit registers, and
+// compares with the reference value c(T) = s T R^{-1} mod N.  c is computed
+// with one modulo at the chunk start and then stepped, c(T+1) = c(T) + s R^{-1}
+// mod N with one conditional subtraction, so no check divides.  The congruence
+// test r = c (mod N) takes a fast path for r - c in {0, -N, +N} and divides
+// only otherwise.  The kernel reads nothing but the table: it is bound by the
+// integer pipes, not by memory.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace montgb {
+namespace {
+
+struct SweepN {
+  int32_t N;
+  uint32_t nprime;   // -N^{-1} mod R
+  uint32_t ninv;     // N^{-1} mod R (two's complement reading gives N^{-1} mods R)
+  uint32_t step;     // s R^{-1} mod N
+  int64_t t_lo;      // first T of this modulus
+  int64_t t_hi;      // last T
+  int32_t r_lo;      // claimed range (inclusive)
+  int32_t r_hi;
+  uint64_t item0;    // index of this modulus's first chunk
+};
+
+struct SweepParams {
+  int log2R;
+  int n;            // log2R / 2 (Plantard family)
+  int alpha;
+  uint32_t chunk;   // T per chunk
+};
+
+template <int V>
+__device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const SweepParams& p) {
+  const uint32_t mask = (1u << p.log2R) - 1u;
+  const int32_t N = e.N;
+  if constexpr (V == MONT_REDC) {
+    // m <- (T mod R) N' mod R;  t <- (T + mN) / R;  if t >= N: t - N
+    const uint32_t m = ((static_cast<uint32_t>(T) & mask) * e.nprime) & mask;
+    const int64_t t = (static_cast<int64_t>(T) + static_cast<int64_t>(m) * N) >> p.log2R;
+    return static_cast<int32_t>(t >= N ? t - N : t);
+  } else if constexpr (V == MONT_SIGNED) {
+    // T = a1 R + a0;  m0 <- a0 N^{-1} mods R;  t <- floor(m0 N / R);  r <- a1 - t
+    const uint32_t a0 = static_cast<uint32_t>(T) & mask;
+    const int32_t a1 = T >> p.log2R;
+    const uint32_t x = (a0 * e.ninv) & mask;
+    const int32_t m0 = x > (mask >> 1) ? static_cast<int32_t>(x) - static_cast<int32_t>(mask) - 1
+                                       : static_cast<int32_t>(x);
+    return a1 - ((m0 * N) >> p.log2R);
+  } else if constexpr (V == MONT_PLANTARD) {
+    // r <- floor((floor((T N^{-1} mod R) / 2^n) + 1) N / 2^n);  if r = N: 0
+    const uint32_t m = (static_cast<uint32_t>(T) * e.ninv) & mask;
+    const int32_t r = static_cast<int32_t>((((m >> p.n) + 1u) * static_cast<uint32_t>(N)) >> p.n);
+    return r == N ? 0 : r;
+  } else {
+    const uint32_t x = (static_cast<uint32_t>(T) * e.ninv) & mask;
+    const int32_t m = x > (mask >> 1) ? static_cast<int32_t>(x) - static_cast<int32_t>(mask) - 1
+                                      : static_cast<int32_t>(x);   // T Ñ^{-1} mods R
+    if constexpr (V == MONT_SIGNED_PLANTARD) {
+      // r <- round(round(m / 2^n) N / 2^n), halves rounded up
+      const int32_t half = 1 << (p.n - 1);
+      const int32_t q = (m + half) >> p.n;
+      return (q * N + half) >> p.n;
+    } else {
+      // r <- floor((floor(m / 2^n) + 2^alpha) N / 2^n)
+      return (((m >> p.n) + (1 << p.alpha)) * N) >> p.n;
+    }
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ tab, int n_tab,
+                                                    uint64_t n_items, SweepParams p,
+                                                    unsigned long long* __restrict__ counts,
+                                                    mont_cex* __restrict__ cex,
+                                                    unsigned long long* __restrict__ cex_n,
+                                                    unsigned long long cap) {
+  constexpr bool kUnsignedTarget = (V == MONT_REDC || V == MONT_PLANTARD);
+  const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t item = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; item < n_items;
+       item += nthreads) {
+    int lo = 0, hi = n_tab - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tab[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    const SweepN e = tab[lo];
+    const int64_t T0 = e.t_lo + static_cast<int64_t>(item - e.item0) * p.chunk;
+    const int64_t T1 = T0 + p.chunk - 1 < e.t_hi ? T0 + p.chunk - 1 : e.t_hi;
+    const uint32_t cnt = static_cast<uint32_t>(T1 - T0 + 1);
+    const uint32_t N = static_cast<uint32_t>(e.N);
+    int64_t tm = T0 % e.N;
+    if (tm < 0) tm += e.N;
+    uint32_t c = static_cast<uint32_t>((static_cast<uint64_t>(tm) * e.step) % N);
+    uint32_t local = 0;
+    bool full = false;  // the example buffer was seen full: stop touching it
+    uint32_t Tu = static_cast<uint32_t>(static_cast<int32_t>(T0));
+    for (uint32_t i = 0; i < cnt; ++i, ++Tu) {
+      const int32_t T = static_cast<int32_t>(Tu);
+      const int32_t r = candidate<V>(T, e, p);
+      const int64_t d = static_cast<int64_t>(r) - static_cast<int64_t>(c);
+      const bool cong = d == 0 || d == -static_cast<int64_t>(N) || d == static_cast<int64_t>(N) ||
+                        (d % static_cast<int64_t>(N)) == 0;
+      const bool bad = !cong || r < e.r_lo || r > e.r_hi;
+      if (bad) {
+        ++local;
+        if (!full && *reinterpret_cast<volatile unsigned long long*>(cex_n) >= cap) full = true;
+        if (!full) {
+          const unsigned long long slot = atomicAdd(cex_n, 1ull);
+          if (slot < cap) {
+            int64_t expect = c;
+            if (!kUnsignedTarget && c > (N - 1u) / 2u) expect -= N;
+            mont_cex rec;
+            rec.N = N;
+            rec.reserved = 0;
+            rec.T = T;
+            rec.r = r;
+            rec.expected = expect;
+            cex[slot] = rec;
+          }
+        }
+      }
+      c += e.step;
+      if (c >= N) c -= N;
+    }
+    if (local) atomicAdd(counts + lo, static_cast<unsigned long long>(local));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+uint32_t inv_pow2_u32(uint32_t N, uint32_t mask) {  // N^{-1} mod 2^k, Newton-Hensel
+  uint32_t x = N;
+  for (int i = 0; i < 5; ++i) x *= 2u - N * x;
+  return x & mask;
+}
+
+int64_t inv_mod(int64_t a, int64_t m) {  // a^{-1} mod m, extended Euclid; gcd(a, m) = 1
+  int64_t r0 = m, r1 = ((a % m) + m) % m, s0 = 0, s1 = 1;
+  while (r1 != 0) {
+    const int64_t q = r0 / r1;
+    int64_t t = r0 - q * r1; r0 = r1; r1 = t;
+    t = s0 - q * s1; s0 = s1; s1 = t;
+  }
+  return ((s0 % m) + m) % m;
+}
+
+bool precondition(int variant, int64_t N, int log2R, int alpha) {
+  const int64_t R = int64_t{1} << log2R;
+  const int n = log2R / 2;
+  switch (variant) {
+    case MONT_REDC: return N < R;
+    case MONT_SIGNED: return 2 * N < R;
+    case MONT_PLANTARD: {  // 5 N^2 < (2^{n+1} - N)^2, N < 2^15 so this fits in 64 bits
+      const int64_t d = (int64_t{1} << (n + 1)) - N;
+      return d > 0 && 5 * N * N < d * d;
+    }
+    case MONT_SIGNED_PLANTARD: return N < (int64_t{1} << (n - 1));
+    case MONT_SIGNED_PLANTARD2:
+      return n - alpha - 1 >= 0 && N < (int64_t{1} << (n - alpha - 1));
+  }
+  return false;
+}
+
+void default_domain(int variant, int64_t N, int log2R, int alpha, int64_t* lo, int64_t* hi) {
+  const int64_t R = int64_t{1} << log2R;
+  const int n = log2R / 2;
+  switch (variant) {
+    case MONT_REDC: *lo = 0; *hi = R * N - 1; return;
+    case MONT_SIGNED: *lo = -(N * R / 2) + 1; *hi = N * R / 2 - 1; return;
+    case MONT_PLANTARD: *lo = 0; *hi = N * N; return;
+    case MONT_SIGNED_PLANTARD: *hi = int64_t{1} << (2 * n - 2); *lo = -*hi; return;
+    default: *hi = (int64_t{1} << (2 * alpha)) * N * N; *lo = -*hi; return;
+  }
+}
+
+void default_range(int variant, int64_t N, int64_t* lo, int64_t* hi) {
+  switch (variant) {
+    case MONT_REDC:
+    case MONT_PLANTARD: *lo = 0; *hi = N - 1; return;
+    case MONT_SIGNED: *lo = -(N - 1); *hi = N - 1; return;
+    default: *lo = -((N - 1) / 2); *hi = (N - 1) / 2; return;
+  }
+}
+
+template <int V>
+cudaError_t launch_sweep(const SweepN* tab, int n_tab, uint64_t n_items, const SweepParams& p,
+                         unsigned long long* counts, mont_cex* cex, unsigned long long* cex_n,
+                         unsigned long long cap, cudaStream_t s) {
+  const int threads = 256;
+  const int per_sm = resident_blocks(reinterpret_cast<const void*>(sweep_kernel<V>), threads);
+  const uint64_t cap_blocks = static_cast<uint64_t>(device_sm_count()) * per_sm;
+  const uint64_t want = (n_items + threads - 1) / threads;
+  const unsigned grid = static_cast<unsigned>(want < cap_blocks ? want : cap_blocks);
+  sweep_kernel<V><<<grid, threads, 0, s>>>(tab, n_tab, n_items, p, counts, cex, cex_n, cap);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Threads of one full-occupancy grid, for sizing chunks.
+static uint64_t resident_threads() { return static_cast<uint64_t>(device_sm_count()) * 2048u; }
+
+}  // namespace montgb
+
+using namespace montgb;
+
+extern "C" int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t N_hi,
+                                 const mont_bounds* claimed, int flags, uint64_t* per_N_counts,
+                                 uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
+                                 size_t* n_cex_total, void* stream) {
+  if (variant < MONT_REDC || variant > MONT_SIGNED_PLANTARD2) return MONT_EINVAL;
+  if (log2R < 2 || log2R > MONT_SWEEP_MAX_LOG2R) return MONT_EINVAL;
+  if (variant >= MONT_PLANTARD && (log2R % 2)) return MONT_EINVAL;
+  if (variant == MONT_SIGNED_PLANTARD2 && (alpha < 0 || alpha > 14)) return MONT_EINVAL;
+  if (N_lo > N_hi || N_hi > MONT_SWEEP_MAX_N || N_hi < 3) return MONT_EINVAL;
+  if (!per_N_counts || !n_cex_total || (cex_cap > 0 && !cex)) return MONT_EINVAL;
+  mont_bounds rules{MONT_DOMAIN_DEFAULT, MONT_RANGE_DEFAULT, 0, 0, 0, 0};
+  if (claimed) rules = *claimed;
+  if (rules.domain_rule < MONT_DOMAIN_DEFAULT || rules.domain_rule > MONT_DOMAIN_EXPLICIT) return MONT_EINVAL;
+  if (rules.range_rule < MONT_RANGE_DEFAULT || rules.range_rule > MONT_RANGE_EXPLICIT) return MONT_EINVAL;
+  const int64_t kMin = INT32_MIN, kMax = INT32_MAX;
+
+  const uint32_t first = (N_lo % 2) ? N_lo : N_lo + 1;
+  const size_t n_odd = first > N_hi ? 0 : (N_hi - first) / 2 + 1;
+  std::vector<SweepN> tab;
+  std::vector<size_t> tab_index;  // position of each table entry among the odd N
+  const uint32_t mask = (1u << log2R) - 1u;
+  const int64_t R = int64_t{1} << log2R;
+  uint64_t total_T = 0;
+  for (size_t i = 0; i < n_odd; ++i) {
+    per_N_counts[i] = 0;
+    if (per_N_checked) per_N_checked[i] = 0;
+  }
+  for (size_t i = 0; i < n_odd; ++i) {
+    const int64_t N = first + 2 * static_cast<int64_t>(i);
+    if (N < 3) continue;
+    if (!(flags & MONT_SWEEP_INCLUDE_OUT_OF_SPEC) && !precondition(variant, N, log2R, alpha)) continue;
+    int64_t tlo, thi, rlo, rhi;
+    if (rules.domain_rule == MONT_DOMAIN_DEFAULT) {
+      default_domain(variant, N, log2R, alpha, &tlo, &thi);
+    } else if (rules.domain_rule == MONT_DOMAIN_REDC) {
+      tlo = 0; thi = R * N - 1;
+    } else {
+      tlo = rules.t_lo; thi = rules.t_hi;
+    }
+    switch (rules.range_rule) {
+      case MONT_RANGE_DEFAULT: default_range(variant, N, &rlo, &rhi); break;
+      case MONT_RANGE_UNSIGNED: rlo = 0; rhi = N - 1; break;
+      case MONT_RANGE_WIDE: rlo = -(N - 1); rhi = N - 1; break;
+      case MONT_RANGE_CENTRED: rlo = -((N - 1) / 2); rhi = (N - 1) / 2; break;
+      default: rlo = rules.r_lo; rhi = rules.r_hi; break;
+    }
+    if (tlo > thi) continue;  // empty domain: nothing checked
+    if (tlo < kMin || thi > kMax || rlo < kMin || rhi > kMax || rlo > rhi) return MONT_EINVAL;
+    SweepN e{};
+    e.N = static_cast<int32_t>(N);
+    e.ninv = inv_pow2_u32(static_cast<uint32_t>(N), mask);
+    e.nprime = (0u - e.ninv) & mask;
+    const int64_t rinv = inv_mod(R % N, N);
+    e.step = static_cast<uint32_t>(variant >= MONT_PLANTARD ? (N - rinv) % N : rinv);
+    e.t_lo = tlo;
+    e.t_hi = thi;
+    e.r_lo = static_cast<int32_t>(rlo);
+    e.r_hi = static_cast<int32_t>(rhi);
+    tab.push_back(e);
+    tab_index.push_back(i);
+    total_T += static_cast<uint64_t>(thi - tlo + 1);
+    if (per_N_checked) per_N_checked[i] = static_cast<uint64_t>(thi - tlo + 1);
+  }
+  *n_cex_total = 0;
+  if (tab.empty()) return MONT_OK;
+
+  // Chunk size: a power of two in [32, 4096] giving >= 8 chunks per resident thread.
+  uint64_t chunk = 4096;
+  while (chunk > 32 && total_T / chunk < 8 * resident_threads()) chunk >>= 1;
+  uint64_t items = 0;
+  for (auto& e : tab) {
+    e.item0 = items;
+    items += (static_cast<uint64_t>(e.t_hi - e.t_lo) + chunk) / chunk;
+  }
+  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk)};
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n_tab = tab.size();
+  const size_t dev_cap = cex_cap;
+  const size_t bytes = n_tab * sizeof(SweepN) + n_tab * sizeof(unsigned long long) +
+                       sizeof(unsigned long long) + dev_cap * sizeof(mont_cex) + 256;
+  void* scratch = nullptr;
+  cudaError_t err = cudaMallocAsync(&scratch, bytes, s);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return err == cudaErrorMemoryAllocation ? MONT_ENOMEM : cuda_status(err);
+  }
+  char* base = static_cast<char*>(scratch);
+  SweepN* d_tab = reinterpret_cast<SweepN*>(base);
+  auto* d_counts = reinterpret_cast<unsigned long long*>(base + n_tab * sizeof(SweepN));
+  auto* d_cex_n = d_counts + n_tab;
+  auto* d_cex = reinterpret_cast<mont_cex*>(
+      (reinterpret_cast<uintptr_t>(d_cex_n + 1) + 15) & ~static_cast<uintptr_t>(15));
+  std::vector<unsigned long long> h_counts(n_tab);
+  unsigned long long h_cex_n = 0;
+  int status = MONT_OK;
+
+  err = cudaMemcpyAsync(d_tab, tab.data(), n_tab * sizeof(SweepN), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_counts, 0, (n_tab + 1) * sizeof(unsigned long long), s);
+  if (err == cudaSuccess) {
+    switch (variant) {
+      case MONT_REDC: err = launch_sweep<MONT_REDC>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
+      case MONT_SIGNED: err = launch_sweep<MONT_SIGNED>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
+      case MONT_PLANTARD: err = launch_sweep<MONT_PLANTARD>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
+      case MONT_SIGNED_PLANTARD: err = launch_sweep<MONT_SIGNED_PLANTARD>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
+      default: err = launch_sweep<MONT_SIGNED_PLANTARD2>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
+    }
+  }
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(h_counts.data(), d_counts, n_tab * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&h_cex_n, d_cex_n, sizeof(h_cex_n), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  size_t n_rec = 0;
+  if (err == cudaSuccess) {
+    n_rec = static_cast<size_t>(h_cex_n < dev_cap ? h_cex_n : dev_cap);
+    if (n_rec)
+      err = cudaMemcpyAsync(cex, d_cex, n_rec * sizeof(mont_cex), cudaMemcpyDeviceToHost, s);
+  }
+  cudaError_t ferr = cudaFreeAsync(scratch, s);
+  if (err == cudaSuccess) err = ferr;
+  cudaError_t serr = cudaStreamSynchronize(s);
+  if (err == cudaSuccess) err = serr;
+  if (err != cudaSuccess) return cuda_status(err);
+
+  uint64_t total = 0;
+  for (size_t j = 0; j < n_tab; ++j) {
+    per_N_counts[tab_index[j]] = h_counts[j];
+    total += h_counts[j];
+  }
+  std::sort(cex, cex + n_rec, [](const mont_cex& a, const mont_cex& b) {
+    return a.N != b.N ? a.N < b.N : a.T < b.T;
+  });
+  *n_cex_total = static_cast<size_t>(total);
+  if (total > cex_cap) status = MONT_EOVERFLOW;
+  return status;
+}

@@ -35,4 +35,13 @@ void set_tuned_shape(int width, int variant, int mode, const LaunchShape& shape)
   g_table[key] = shape;
 }
 
+LaunchShape tuned_batched_shape(int width) {
+  // mode -1 marks the batched kernel in the table
+  return tuned_shape(width, -1, -1);
+}
+
+void set_tuned_batched_shape(int width, const LaunchShape& shape) {
+  set_tuned_shape(width, -1, -1, shape);
+}
+
 }  // namespace montgb

@@ -175,10 +175,6 @@ __global__ void __launch_bounds__(512) word_kernel(const void* __restrict__ xp,
   for (size_t i = done + tid; i < n; i += nthreads) scalar_element<Op, M>(xp, yp, op, i, c);
 }
 
-// Occupancy-derived resident blocks per SM of a kernel (cached per kernel,
-// block size and device; defined in api.cu).
-int resident_blocks(const void* kernel, int threads);
-
 template <class Op, Mode M, int VB, int U>
 cudaError_t launch_one(const typename Op::C& c, const void* x, const void* y, void* out, size_t n,
                        cudaStream_t s, const LaunchShape& shape) {

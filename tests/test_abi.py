@@ -158,3 +158,22 @@ def test_product_path_has_no_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(mg, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         mg.lib()
+
+
+def test_sweep_argument_checks_need_no_gpu(L):
+    import ctypes as C
+    counts = (C.c_uint64 * 4096)()
+    total = C.c_size_t()
+    bad = [(0, 17, 0, 3, 31), (2, 15, 0, 3, 31), (0, 16, 0, 40, 30), (0, 16, 0, 3, 40000),
+           (7, 16, 0, 3, 31), (4, 16, 15, 3, 31)]
+    for v, l, a, lo, hi in bad:
+        assert L.mont_verify_sweep(v, l, a, lo, hi, None, 0, counts, None, None, 0,
+                                   C.byref(total), None) == mg.MONT_EINVAL
+    # every N out of spec and skipped: nothing to launch, all counts zero
+    assert L.mont_verify_sweep(2, 8, 0, 21, 31, None, 0, counts, None, None, 0,
+                               C.byref(total), None) == mg.MONT_OK
+    assert total.value == 0 and all(counts[i] == 0 for i in range(6))
+    # an explicit domain outside 32-bit T is refused
+    b = mg.MontBounds(mg.MONT_DOMAIN_EXPLICIT, mg.MONT_RANGE_DEFAULT, 0, 1 << 40, 0, 0)
+    assert L.mont_verify_sweep(0, 16, 0, 3, 31, C.byref(b), 0, counts, None, None, 0,
+                               C.byref(total), None) == mg.MONT_EINVAL
