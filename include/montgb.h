@@ -294,6 +294,52 @@ int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t
                       uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
                       size_t* n_cex_total, void* stream);
 
+/* ------------------------------------------------------------ autotuner */
+/*
+ * Launch shapes.  Every kernel family has a few launch knobs; a per-process
+ * table maps (current device, word width in bits, variant, mode) to a shape,
+ * and entries that are not set use built-in defaults.  Shapes change speed
+ * only, never results.
+ */
+typedef struct mont_launch_shape {
+  int threads;        /* threads per block: 64..512 (word kernels), 128 or 256 (others) */
+  int unroll;         /* 256-bit vectors in flight per thread per operand: 1, 2 or 4      */
+  int vec_bytes;      /* word kernels: 32, 16 or 0 (scalar loads)                         */
+  int blocks_per_sm;  /* resident blocks per SM the grid is sized for; 0 = occupancy max   */
+  int tile_iters;     /* reserved; keep 0                                                   */
+  int team;           /* multi-limb: lanes per element (1, 2, 4, 8, 16); 0 = default       */
+} mont_launch_shape;
+
+#define MONT_TUNE_MODE_MUL          0  /* mont_mul (also used by the other modes when tuned) */
+#define MONT_TUNE_MODE_TO_DOMAIN    1
+#define MONT_TUNE_MODE_FROM_DOMAIN  2
+#define MONT_TUNE_MODE_REDC         3
+#define MONT_TUNE_MODE_BATCHED     (-1)  /* mont_mul_batched; variant is ignored */
+
+/* Set (or, with shape = NULL, clear) the shape of one table entry for the
+ * current device.  MONT_EINVAL for out-of-range knobs. */
+int mont_tune_set(int width_bits, int variant, int mode, const mont_launch_shape* shape);
+/* The shape the library would use now for that entry (defaults filled in). */
+int mont_tune_get(int width_bits, int variant, int mode, mont_launch_shape* shape);
+
+#define MONT_TUNE_ELEMENTWISE 1  /* tune mont_mul and the domain maps of ctx's width/variant */
+#define MONT_TUNE_BATCHED     2  /* tune mont_mul_batched for ctx's word width             */
+
+/*
+ * mont_autotune -- time every candidate shape on n elements of ctx's type,
+ * with CUDA events on `stream`, and record the fastest in the table.
+ * Allocates 3 n elements of device scratch on `stream` and frees it before
+ * returning; synchronous.  Timing uses arbitrary operand bits, which is safe:
+ * the kernels have no data-dependent memory access.
+ */
+int mont_autotune(mont_ctx_t ctx, size_t n, int flags, void* stream);
+
+/* Persist the current device's table entries to a text file / load the
+ * entries of a file whose device name and SM count match the current device
+ * (others are ignored).  MONT_EINVAL on I/O or format errors. */
+int mont_tune_save(const char* path);
+int mont_tune_load(const char* path);
+
 /* ------------------------------------------------------------- utilities */
 /* Static description of a status code; never NULL. */
 const char* mont_strerror(int status);

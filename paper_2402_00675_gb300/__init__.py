@@ -66,6 +66,21 @@ class MontCex(ctypes.Structure):
                 ("r", ctypes.c_int64), ("expected", ctypes.c_int64)]
 
 
+MONT_TUNE_MODE_MUL = 0
+MONT_TUNE_MODE_TO_DOMAIN = 1
+MONT_TUNE_MODE_FROM_DOMAIN = 2
+MONT_TUNE_MODE_REDC = 3
+MONT_TUNE_MODE_BATCHED = -1
+MONT_TUNE_ELEMENTWISE = 1
+MONT_TUNE_BATCHED = 2
+
+
+class MontLaunchShape(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("unroll", ctypes.c_int), ("vec_bytes", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("tile_iters", ctypes.c_int),
+                ("team", ctypes.c_int)]
+
+
 class MontError(RuntimeError):
     """A non-zero status from the C ABI."""
 
@@ -122,6 +137,11 @@ def _declare(L):
         "mont_batch_launch": (_int, [_vp, _vp]),
         "mont_batch_update": (_int, [_vp, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
         "mont_batch_destroy": (_int, [_vp]),
+        "mont_tune_set": (_int, [_int, _int, _int, _c.POINTER(MontLaunchShape)]),
+        "mont_tune_get": (_int, [_int, _int, _int, _c.POINTER(MontLaunchShape)]),
+        "mont_autotune": (_int, [_vp, _sz, _int, _vp]),
+        "mont_tune_save": (_int, [_c.c_char_p]),
+        "mont_tune_load": (_int, [_c.c_char_p]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -368,6 +388,32 @@ def mont_verify_sweep(variant: int, log2R: int, alpha: int, N_lo: int, N_hi: int
     return SweepResult(moduli, {N: int(counts[i]) for i, N in enumerate(moduli)},
                        {N: int(checked[i]) for i, N in enumerate(moduli)}, ex, total.value,
                        st == MONT_EOVERFLOW)
+
+
+def mont_tune_set(width_bits: int, variant: int, mode: int, shape: dict | None) -> None:
+    """Set (or clear, with shape=None) one launch-shape table entry."""
+    ptr = None
+    if shape is not None:
+        ptr = ctypes.byref(MontLaunchShape(**{k: int(v) for k, v in shape.items()}))
+    _check(lib().mont_tune_set(width_bits, variant, mode, ptr), "mont_tune_set")
+
+
+def mont_tune_get(width_bits: int, variant: int, mode: int) -> dict:
+    sh = MontLaunchShape()
+    _check(lib().mont_tune_get(width_bits, variant, mode, ctypes.byref(sh)), "mont_tune_get")
+    return {k: getattr(sh, k) for k, _ in MontLaunchShape._fields_}
+
+
+def mont_autotune(ctx: Ctx, n: int, flags: int = MONT_TUNE_ELEMENTWISE, stream=None) -> None:
+    _check(lib().mont_autotune(ctx, n, flags, _stream(stream)), "mont_autotune")
+
+
+def mont_tune_save(path: str) -> None:
+    _check(lib().mont_tune_save(path.encode()), "mont_tune_save")
+
+
+def mont_tune_load(path: str) -> None:
+    _check(lib().mont_tune_load(path.encode()), "mont_tune_load")
 
 
 def mont_sync(stream=None) -> None:

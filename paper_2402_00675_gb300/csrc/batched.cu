@@ -4,12 +4,21 @@
 // (operand pointers, length, the modulus's constants, the variant) travel by
 // value in the kernel's parameter space (up to 32 KB on sm_90 and later), so
 // the call needs no device memory and no upload; each CTA stages the
-// descriptors in shared memory once and then walks "tiles" round-robin: tile
-// t is `tile_elems` consecutive elements of one vector, found by a binary
-// search over the descriptors' first-tile indices.  Inside a tile the CTA
-// streams the operands exactly like the element-wise kernel (256-bit loads,
-// U vectors in flight per thread) and applies that vector's variant; the
-// variant switch is uniform across the CTA.
+// descriptors in shared memory once.
+//
+// Load balance: the vectors are laid end to end in one flat element index
+// space of total length L, and CTA c owns the contiguous slice
+// [c S, (c + 1) S) with S = ceil(L / grid), rounded to whole 256-bit vectors.
+// A slice may span several vectors; the CTA finds the first by binary search
+// over the descriptors' flat offsets and walks forward.  Every CTA therefore
+// moves the same number of bytes, whatever the length mix.  Inside a slice
+// the CTA streams the operands like the element-wise kernel (256-bit loads, U
+// vectors in flight per thread), with scalar heads and tails where a slice
+// boundary cuts a 256-bit vector.
+//
+// A batch whose vectors all use one variant runs a kernel specialised for
+// it; a mixed batch runs a kernel that switches per vector (uniform across
+// the CTA) into out-of-line per-variant bodies.
 //
 // mont_batch_* wrap the launches of one batch in a CUDA graph built once and
 // replayed; new operand pointers for the same shapes update the graph's
@@ -17,6 +26,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "tune.h"
@@ -33,7 +43,7 @@ struct BatchDesc {
   const void* b;
   void* out;
   uint64_t len;
-  uint64_t tile0;   // index of this vector's first tile
+  uint64_t elem0;   // offset of this vector in the flat element space
   C c;              // constants of the modulus
   int32_t variant;
   int32_t vec_ok;   // all three pointers 32-byte aligned
@@ -42,30 +52,38 @@ struct BatchDesc {
 template <class C>
 struct BatchParams {
   int32_t count;
-  uint32_t tile_elems;
-  uint64_t total_tiles;
+  int32_t uniform_variant;  // the variant of every vector, or -1 for a mix
+  uint64_t total;           // sum of the lengths
+  uint64_t per_cta;         // slice length S
   BatchDesc<C> d[kMaxDesc];
 };
 
-// Elements [off, off + cnt) of one vector; off is a multiple of the tile size.
+// Elements [o0, o1) of one vector.
 template <class Op, int VB, int U>
-__device__ __forceinline__ void tile_body(const BatchDesc<typename Op::C>& d, uint64_t off,
-                                          uint64_t cnt) {
+__device__ __forceinline__ void segment(const BatchDesc<typename Op::C>& d, uint64_t o0,
+                                        uint64_t o1) {
   using E = typename Op::E;
   using TT = typename Op::TT;
   constexpr int EPV = VB / static_cast<int>(sizeof(E));
-  uint64_t done = 0;
+  uint64_t v_lo = 0, v_hi = 0;  // whole 256-bit vectors [v_lo, v_hi) inside [o0, o1)
   if (d.vec_ok) {
-    const char* a = static_cast<const char*>(d.a) + off * sizeof(E);
-    const char* b = static_cast<const char*>(d.b) + off * sizeof(E);
-    char* o = static_cast<char*>(d.out) + off * sizeof(E);
-    const uint64_t nv = cnt / EPV;
-    for (uint64_t base = 0; base < nv; base += static_cast<uint64_t>(blockDim.x) * U) {
+    v_lo = (o0 + EPV - 1) / EPV;
+    v_hi = o1 / EPV;
+    if (v_hi < v_lo) v_hi = v_lo;
+  }
+  const uint64_t h_end = v_hi > v_lo ? v_lo * EPV : o1;   // scalar head [o0, h_end)
+  for (uint64_t i = o0 + threadIdx.x; i < h_end; i += blockDim.x)
+    scalar_element<Op, Mode::kMul>(d.a, d.b, d.out, i, d.c);
+  if (v_hi > v_lo) {
+    const char* a = static_cast<const char*>(d.a);
+    const char* b = static_cast<const char*>(d.b);
+    char* o = static_cast<char*>(d.out);
+    for (uint64_t base = v_lo; base < v_hi; base += static_cast<uint64_t>(blockDim.x) * U) {
       Vec<VB> va[U], vb[U];
 #pragma unroll
       for (int j = 0; j < U; ++j) {
         const uint64_t v = base + threadIdx.x + static_cast<uint64_t>(j) * blockDim.x;
-        if (v < nv) {
+        if (v < v_hi) {
           vld(va[j], a + v * VB);
           vld(vb[j], b + v * VB);
         }
@@ -73,7 +91,7 @@ __device__ __forceinline__ void tile_body(const BatchDesc<typename Op::C>& d, ui
 #pragma unroll
       for (int j = 0; j < U; ++j) {
         const uint64_t v = base + threadIdx.x + static_cast<uint64_t>(j) * blockDim.x;
-        if (v < nv) {
+        if (v < v_hi) {
           Vec<VB> vo;
 #pragma unroll
           for (int e = 0; e < EPV; ++e)
@@ -83,14 +101,41 @@ __device__ __forceinline__ void tile_body(const BatchDesc<typename Op::C>& d, ui
         }
       }
     }
-    done = nv * EPV;
+    for (uint64_t i = v_hi * EPV + threadIdx.x; i < o1; i += blockDim.x)   // scalar tail
+      scalar_element<Op, Mode::kMul>(d.a, d.b, d.out, i, d.c);
   }
-  for (uint64_t i = done + threadIdx.x; i < cnt; i += blockDim.x)
-    scalar_element<Op, Mode::kMul>(d.a, d.b, d.out, off + i, d.c);
+}
+
+template <class Op, int VB, int U>
+__device__ __noinline__ void segment_outlined(const BatchDesc<typename Op::C>& d, uint64_t o0,
+                                              uint64_t o1) {
+  segment<Op, VB, U>(d, o0, o1);
 }
 
 template <class C, int VB, int U>
-__global__ void __launch_bounds__(512) batched_kernel(const __grid_constant__ BatchParams<C> p) {
+__device__ __forceinline__ void segment_mixed(const BatchDesc<C>& d, uint64_t o0, uint64_t o1) {
+  if constexpr (sizeof(C) == sizeof(WordConst64)) {
+    switch (d.variant) {
+      case MONT_REDC: segment_outlined<Redc64, VB, U>(d, o0, o1); break;
+      case MONT_SIGNED: segment_outlined<Signed64, VB, U>(d, o0, o1); break;
+      case MONT_PLANTARD: segment_outlined<Plantard64, VB, U>(d, o0, o1); break;
+      case MONT_SIGNED_PLANTARD: segment_outlined<SignedPlantard64, VB, U>(d, o0, o1); break;
+      default: segment_outlined<SignedPlantard2_64, VB, U>(d, o0, o1); break;
+    }
+  } else {
+    switch (d.variant) {
+      case MONT_REDC: segment_outlined<Redc32, VB, U>(d, o0, o1); break;
+      case MONT_SIGNED: segment_outlined<Signed32, VB, U>(d, o0, o1); break;
+      case MONT_PLANTARD: segment_outlined<Plantard32, VB, U>(d, o0, o1); break;
+      case MONT_SIGNED_PLANTARD: segment_outlined<SignedPlantard32, VB, U>(d, o0, o1); break;
+      default: segment_outlined<SignedPlantard2_32, VB, U>(d, o0, o1); break;
+    }
+  }
+}
+
+// Op = void: mixed variants.
+template <class C, class Op, int VB, int U>
+__global__ void __launch_bounds__(256, (U >= 4 ? 2 : 4)) batched_kernel(const __grid_constant__ BatchParams<C> p) {
   extern __shared__ __align__(16) unsigned char smem[];
   auto* sd = reinterpret_cast<BatchDesc<C>*>(smem);
   {
@@ -100,32 +145,24 @@ __global__ void __launch_bounds__(512) batched_kernel(const __grid_constant__ Ba
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
-  for (uint64_t tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x) {
-    int lo = 0, hi = p.count - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (sd[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-    }
-    const BatchDesc<C>& d = sd[lo];
-    const uint64_t off = (tile - d.tile0) * p.tile_elems;
-    const uint64_t rest = d.len - off;
-    const uint64_t cnt = rest < p.tile_elems ? rest : p.tile_elems;
-    if constexpr (sizeof(C) == sizeof(WordConst64)) {
-      switch (d.variant) {
-        case MONT_REDC: tile_body<Redc64, VB, U>(d, off, cnt); break;
-        case MONT_SIGNED: tile_body<Signed64, VB, U>(d, off, cnt); break;
-        case MONT_PLANTARD: tile_body<Plantard64, VB, U>(d, off, cnt); break;
-        case MONT_SIGNED_PLANTARD: tile_body<SignedPlantard64, VB, U>(d, off, cnt); break;
-        default: tile_body<SignedPlantard2_64, VB, U>(d, off, cnt); break;
-      }
+  const uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * p.per_cta;
+  if (g0 >= p.total) return;
+  const uint64_t g1 = g0 + p.per_cta < p.total ? g0 + p.per_cta : p.total;
+  int lo = 0, hi = p.count - 1;   // last vector with elem0 <= g0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sd[mid].elem0 <= g0) lo = mid; else hi = mid - 1;
+  }
+  for (int j = lo; j < p.count && sd[j].elem0 < g1; ++j) {
+    const BatchDesc<C>& d = sd[j];
+    const uint64_t s0 = g0 > d.elem0 ? g0 : d.elem0;
+    const uint64_t e = d.elem0 + d.len;
+    const uint64_t s1 = g1 < e ? g1 : e;
+    if (s1 <= s0) continue;
+    if constexpr (std::is_void_v<Op>) {
+      segment_mixed<C, VB, U>(d, s0 - d.elem0, s1 - d.elem0);
     } else {
-      switch (d.variant) {
-        case MONT_REDC: tile_body<Redc32, VB, U>(d, off, cnt); break;
-        case MONT_SIGNED: tile_body<Signed32, VB, U>(d, off, cnt); break;
-        case MONT_PLANTARD: tile_body<Plantard32, VB, U>(d, off, cnt); break;
-        case MONT_SIGNED_PLANTARD: tile_body<SignedPlantard32, VB, U>(d, off, cnt); break;
-        default: tile_body<SignedPlantard2_32, VB, U>(d, off, cnt); break;
-      }
+      segment<Op, VB, U>(d, s0 - d.elem0, s1 - d.elem0);
     }
   }
 }
@@ -141,16 +178,34 @@ struct Group {
   int threads = 256;
   size_t smem = 0;
   const void* kernel = nullptr;
-  uint64_t tiles() const { return width == 32 ? p32.total_tiles : p64.total_tiles; }
+  uint64_t total() const { return width == 32 ? p32.total : p64.total; }
   void* params() { return width == 32 ? static_cast<void*>(&p32) : static_cast<void*>(&p64); }
 };
 
-template <class C>
-const void* kernel_for(int unroll) {
+template <class C, class Op>
+const void* kernel_u(int unroll) {
   switch (unroll) {
-    case 1: return reinterpret_cast<const void*>(batched_kernel<C, 32, 1>);
-    case 4: return reinterpret_cast<const void*>(batched_kernel<C, 32, 4>);
-    default: return reinterpret_cast<const void*>(batched_kernel<C, 32, 2>);
+    case 1: return reinterpret_cast<const void*>(batched_kernel<C, Op, 32, 1>);
+    case 4: return reinterpret_cast<const void*>(batched_kernel<C, Op, 32, 4>);
+    default: return reinterpret_cast<const void*>(batched_kernel<C, Op, 32, 2>);
+  }
+}
+
+template <class C>
+const void* kernel_for(int variant, int unroll) {
+  constexpr bool w64 = sizeof(C) == sizeof(WordConst64);
+  using R = std::conditional_t<w64, Redc64, Redc32>;
+  using S = std::conditional_t<w64, Signed64, Signed32>;
+  using P = std::conditional_t<w64, Plantard64, Plantard32>;
+  using S1 = std::conditional_t<w64, SignedPlantard64, SignedPlantard32>;
+  using S2 = std::conditional_t<w64, SignedPlantard2_64, SignedPlantard2_32>;
+  switch (variant) {
+    case MONT_REDC: return kernel_u<C, R>(unroll);
+    case MONT_SIGNED: return kernel_u<C, S>(unroll);
+    case MONT_PLANTARD: return kernel_u<C, P>(unroll);
+    case MONT_SIGNED_PLANTARD: return kernel_u<C, S1>(unroll);
+    case MONT_SIGNED_PLANTARD2: return kernel_u<C, S2>(unroll);
+    default: return kernel_u<C, void>(unroll);
   }
 }
 
@@ -168,16 +223,27 @@ void fill(BatchParams<C>& p, const C& c, int variant, const void* a, const void*
   d.vec_ok = al(a) && al(b) && al(o) ? 1 : 0;
 }
 
+// Flat offsets, the common variant and the slice length for `grid` CTAs.
 template <class C>
-void finish(BatchParams<C>& p, int count, uint32_t tile_elems) {
+void finish(BatchParams<C>& p, int count) {
   p.count = count;
-  p.tile_elems = tile_elems;
   uint64_t t = 0;
+  int uv = -2;
   for (int i = 0; i < count; ++i) {
-    p.d[i].tile0 = t;
-    t += (p.d[i].len + tile_elems - 1) / tile_elems;
+    p.d[i].elem0 = t;
+    t += p.d[i].len;
+    if (p.d[i].len == 0) continue;
+    uv = (uv == -2 || uv == p.d[i].variant) ? p.d[i].variant : -1;
   }
-  p.total_tiles = t;
+  p.total = t;
+  p.uniform_variant = uv < 0 ? -1 : uv;
+}
+
+template <class C>
+void slice(BatchParams<C>& p, unsigned grid, uint64_t quantum) {
+  uint64_t s = (p.total + grid - 1) / grid;
+  s = (s + quantum - 1) / quantum * quantum;
+  p.per_cta = s > 0 ? s : quantum;
 }
 
 // Validate the batch and cut it into launch groups.
@@ -196,10 +262,8 @@ int plan_groups(const mont_ctx_t* ctxs, const void* const* a, const void* const*
       if (reinterpret_cast<uintptr_t>(q) % esize) return MONT_EINVAL;
   }
   const LaunchShape shape = tuned_batched_shape(width);
-  // one tile = tile_iters CTA iterations of `unroll` 256-bit vectors per thread
-  const uint32_t tile_elems = static_cast<uint32_t>(shape.threads) * shape.unroll *
-                              static_cast<uint32_t>(32 / esize) *
-                              static_cast<uint32_t>(shape.tile_iters > 0 ? shape.tile_iters : 1);
+  // slices are whole multiples of one CTA iteration when possible
+  const uint64_t epv = 32 / esize;
   for (int start = 0; start < count; start += kMaxDesc) {
     const int n = std::min(kMaxDesc, count - start);
     Group g;
@@ -212,19 +276,27 @@ int plan_groups(const mont_ctx_t* ctxs, const void* const* a, const void* const*
       else
         fill(g.p64, ctxs[k]->w64, ctxs[k]->variant, a[k], b[k], out[k], lens[k], i);
     }
+    int uv;
     if (width == 32) {
-      finish(g.p32, n, tile_elems);
+      finish(g.p32, n);
+      uv = g.p32.uniform_variant;
       g.smem = n * sizeof(BatchDesc<WordConst32>);
-      g.kernel = kernel_for<WordConst32>(shape.unroll);
+      g.kernel = kernel_for<WordConst32>(uv, shape.unroll);
     } else {
-      finish(g.p64, n, tile_elems);
+      finish(g.p64, n);
+      uv = g.p64.uniform_variant;
       g.smem = n * sizeof(BatchDesc<WordConst64>);
-      g.kernel = kernel_for<WordConst64>(shape.unroll);
+      g.kernel = kernel_for<WordConst64>(uv, shape.unroll);
     }
-    if (g.tiles() == 0) continue;
-    const int per_sm = resident_blocks(g.kernel, g.threads);
+    if (g.total() == 0) continue;
+    const int per_sm = shape.blocks_per_sm > 0 ? shape.blocks_per_sm
+                                               : resident_blocks(g.kernel, g.threads);
     const uint64_t cap = static_cast<uint64_t>(device_sm_count()) * per_sm;
-    g.grid = static_cast<unsigned>(std::min<uint64_t>(cap, g.tiles()));
+    // at least one CTA iteration of work per CTA
+    const uint64_t min_slice = static_cast<uint64_t>(g.threads) * shape.unroll * epv;
+    const uint64_t want = (g.total() + min_slice - 1) / min_slice;
+    g.grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(cap, want)));
+    if (width == 32) slice(g.p32, g.grid, epv); else slice(g.p64, g.grid, epv);
     groups->push_back(g);
   }
   return MONT_OK;

@@ -53,6 +53,7 @@ struct LaunchShape {
   int vec_bytes = 32;       // 32 (256-bit), 16 (128-bit) or 0 (scalar path)
   int blocks_per_sm = 0;    // 0: as many as the occupancy calculator allows
   int tile_iters = 2;       // batched kernel: CTA iterations per tile
+  int team = 0;             // multi-limb: lanes per element (0: default for k)
 };
 
 enum class Mode : int { kMul = 0, kToDomain = 1, kFromDomain = 2, kRedc = 3 };

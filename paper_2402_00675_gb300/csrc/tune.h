@@ -2,6 +2,7 @@
 #pragma once
 
 #include "internal.h"
+#include "montgb.h"
 
 namespace montgb {
 

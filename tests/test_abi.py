@@ -177,3 +177,15 @@ def test_sweep_argument_checks_need_no_gpu(L):
     b = mg.MontBounds(mg.MONT_DOMAIN_EXPLICIT, mg.MONT_RANGE_DEFAULT, 0, 1 << 40, 0, 0)
     assert L.mont_verify_sweep(0, 16, 0, 3, 31, C.byref(b), 0, counts, None, None, 0,
                                C.byref(total), None) == mg.MONT_EINVAL
+
+
+def test_tune_table_set_get_without_gpu(L):
+    mg.mont_tune_set(32, 1, 0, {"threads": 128, "unroll": 4, "vec_bytes": 16})
+    got = mg.mont_tune_get(32, 1, 0)
+    assert (got["threads"], got["unroll"], got["vec_bytes"]) == (128, 4, 16)
+    with pytest.raises(mg.MontError):
+        mg.mont_tune_set(32, 1, 0, {"threads": 100, "unroll": 2, "vec_bytes": 32})
+    with pytest.raises(mg.MontError):
+        mg.mont_tune_set(32, 1, 7, {"threads": 128})
+    mg.mont_tune_set(32, 1, 0, None)
+    assert mg.mont_tune_get(32, 1, 0)["threads"] == 256
