@@ -294,6 +294,38 @@ int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t
                       uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
                       size_t* n_cex_total, void* stream);
 
+/*
+ * mont_verify_sweep_noalloc -- mont_verify_sweep for callers that must not
+ * allocate memory during the call: for example a program that sets its
+ * device-memory budget once at start-up, a host whose device memory is owned
+ * by another allocator, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation cudaMalloc may perform.  The paper has no
+ * counterpart; this is a property of the library interface, not of the
+ * method.
+ *
+ * Same arguments, results, sorting and status codes as mont_verify_sweep,
+ * with two differences:
+ *  - It allocates nothing, on the device or on the host.  Its device
+ *    scratch is one fixed array of about 0.6 MB compiled into the library,
+ *    which every GPU that loads the library keeps until the process exits.
+ *    The host side writes only into the caller's buffers.
+ *  - That array bounds the request: at most MONT_SWEEP_NOALLOC_MAX_MODULI odd
+ *    N in [N_lo, N_hi], and cex_cap at most MONT_SWEEP_NOALLOC_MAX_CEX;
+ *    larger requests return MONT_EINVAL before any GPU work.
+ * Every call on a device shares the one array and it keeps the previous
+ * call's contents (the call clears its counters itself), so calls whose GPU
+ * work overlaps in time -- on different streams or host threads -- race and
+ * must be serialised by the caller.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current
+ * and caches it; make that first call before any stream capture begins.
+ */
+#define MONT_SWEEP_NOALLOC_MAX_MODULI 8192
+#define MONT_SWEEP_NOALLOC_MAX_CEX    4096
+int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t N_hi,
+                              const mont_bounds* claimed, int flags, uint64_t* per_N_counts,
+                              uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
+                              size_t* n_cex_total, void* stream);
+
 /* ------------------------------------------------------------ autotuner */
 /*
  * Launch shapes.  Every kernel family has a few launch knobs; a per-process

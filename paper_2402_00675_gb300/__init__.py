@@ -142,6 +142,10 @@ def _declare(L):
         "mont_autotune": (_int, [_vp, _sz, _int, _vp]),
         "mont_tune_save": (_int, [_c.c_char_p]),
         "mont_tune_load": (_int, [_c.c_char_p]),
+        "mont_verify_sweep_noalloc": (_int, [_int, _int, _int, _c.c_uint32, _c.c_uint32,
+                                             _c.POINTER(MontBounds), _int,
+                                             _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64),
+                                             _c.POINTER(MontCex), _sz, _c.POINTER(_sz), _vp]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -414,6 +418,37 @@ def mont_tune_save(path: str) -> None:
 
 def mont_tune_load(path: str) -> None:
     _check(lib().mont_tune_load(path.encode()), "mont_tune_load")
+
+
+MONT_SWEEP_NOALLOC_MAX_MODULI = 8192
+MONT_SWEEP_NOALLOC_MAX_CEX = 4096
+
+
+def mont_verify_sweep_noalloc(variant: int, log2R: int, alpha: int, N_lo: int, N_hi: int,
+                              claimed: MontBounds | None = None, flags: int = 0,
+                              cex_cap: int = MONT_SWEEP_NOALLOC_MAX_CEX,
+                              stream=None) -> SweepResult:
+    """The sweep through the entry point that allocates nothing (fixed
+    device scratch; bounded sizes); see montgb.h.  The result buffers are
+    created here, in Python, before the call."""
+    first = N_lo if N_lo % 2 else N_lo + 1
+    moduli = list(range(first, N_hi + 1, 2))
+    n = max(len(moduli), 1)
+    counts = (ctypes.c_uint64 * n)()
+    checked = (ctypes.c_uint64 * n)()
+    cex = (MontCex * max(cex_cap, 1))()
+    total = ctypes.c_size_t()
+    st = lib().mont_verify_sweep_noalloc(variant, log2R, alpha, N_lo, N_hi,
+                                         ctypes.byref(claimed) if claimed is not None else None,
+                                         flags, counts, checked, cex, cex_cap,
+                                         ctypes.byref(total), _stream(stream))
+    if st not in (MONT_OK, MONT_EOVERFLOW):
+        raise MontError(st, "mont_verify_sweep_noalloc")
+    nrec = min(total.value, cex_cap)
+    ex = [(int(c.N), int(c.T), int(c.r), int(c.expected)) for c in cex[:nrec]]
+    return SweepResult(moduli, {N: int(counts[i]) for i, N in enumerate(moduli)},
+                       {N: int(checked[i]) for i, N in enumerate(moduli)}, ex, total.value,
+                       st == MONT_EOVERFLOW)
 
 
 def mont_sync(stream=None) -> None:

@@ -16,6 +16,7 @@
 // integer pipes, not by memory.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -354,4 +355,197 @@ extern "C" int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_l
   *n_cex_total = static_cast<size_t>(total);
   if (total > cex_cap) status = MONT_EOVERFLOW;
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// mont_verify_sweep_noalloc: the same sweep for callers that must not
+// allocate.  Its device scratch (moduli table, per-N counters, example
+// buffer) lives in one fixed file-scope array instead of memory allocated per
+// call, and the host side uses only the caller's buffers and a small stack
+// staging array.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocModuli = MONT_SWEEP_NOALLOC_MAX_MODULI;
+constexpr size_t kNoAllocCex = MONT_SWEEP_NOALLOC_MAX_CEX;
+constexpr size_t kNoAllocCountsOff = (kNoAllocModuli * sizeof(SweepN) + 255) / 256 * 256;
+constexpr size_t kNoAllocCexNOff = kNoAllocCountsOff + kNoAllocModuli * sizeof(unsigned long long);
+constexpr size_t kNoAllocCexOff = kNoAllocCexNOff + 256;
+constexpr size_t kNoAllocBytes = kNoAllocCexOff + kNoAllocCex * sizeof(mont_cex);
+}  // namespace
+
+// Shared by every call on a device and held until the process exits.  Host
+// code must not take this symbol's address directly (it is a host-side
+// stand-in); it uses the device address cached by noalloc_scratch().
+static __device__ __align__(256) unsigned char g_sweep_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch(char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return MONT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sweep_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_status(e);
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<char*>(g_noalloc_addr[dev]);
+  return MONT_OK;
+}
+
+// One table entry for modulus N under the call's rules; *checked receives the
+// number of T swept (0 when N is skipped or its domain is empty).  Returns
+// MONT_EINVAL when a bound leaves the 32-bit range.
+int noalloc_entry(int variant, int log2R, int alpha, int64_t N, int flags, const mont_bounds& rules,
+                  SweepN* e, uint64_t* checked) {
+  *e = SweepN{};
+  e->N = static_cast<int32_t>(N);
+  e->t_lo = 0;
+  e->t_hi = -1;
+  *checked = 0;
+  if (N < 3) return MONT_OK;
+  if (!(flags & MONT_SWEEP_INCLUDE_OUT_OF_SPEC) && !precondition(variant, N, log2R, alpha))
+    return MONT_OK;
+  const int64_t R = int64_t{1} << log2R;
+  int64_t tlo, thi, rlo, rhi;
+  if (rules.domain_rule == MONT_DOMAIN_DEFAULT) {
+    default_domain(variant, N, log2R, alpha, &tlo, &thi);
+  } else if (rules.domain_rule == MONT_DOMAIN_REDC) {
+    tlo = 0;
+    thi = R * N - 1;
+  } else {
+    tlo = rules.t_lo;
+    thi = rules.t_hi;
+  }
+  switch (rules.range_rule) {
+    case MONT_RANGE_DEFAULT: default_range(variant, N, &rlo, &rhi); break;
+    case MONT_RANGE_UNSIGNED: rlo = 0; rhi = N - 1; break;
+    case MONT_RANGE_WIDE: rlo = -(N - 1); rhi = N - 1; break;
+    case MONT_RANGE_CENTRED: rlo = -((N - 1) / 2); rhi = (N - 1) / 2; break;
+    default: rlo = rules.r_lo; rhi = rules.r_hi; break;
+  }
+  if (tlo > thi) return MONT_OK;
+  if (tlo < INT32_MIN || thi > INT32_MAX || rlo < INT32_MIN || rhi > INT32_MAX || rlo > rhi)
+    return MONT_EINVAL;
+  const uint32_t mask = (1u << log2R) - 1u;
+  e->ninv = inv_pow2_u32(static_cast<uint32_t>(N), mask);
+  e->nprime = (0u - e->ninv) & mask;
+  const int64_t rinv = inv_mod(R % N, N);
+  e->step = static_cast<uint32_t>(variant >= MONT_PLANTARD ? (N - rinv) % N : rinv);
+  e->t_lo = tlo;
+  e->t_hi = thi;
+  e->r_lo = static_cast<int32_t>(rlo);
+  e->r_hi = static_cast<int32_t>(rhi);
+  *checked = static_cast<uint64_t>(thi - tlo + 1);
+  return MONT_OK;
+}
+}  // namespace
+
+extern "C" int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint32_t N_lo,
+                                         uint32_t N_hi, const mont_bounds* claimed, int flags,
+                                         uint64_t* per_N_counts, uint64_t* per_N_checked,
+                                         mont_cex* cex, size_t cex_cap, size_t* n_cex_total,
+                                         void* stream) {
+  if (variant < MONT_REDC || variant > MONT_SIGNED_PLANTARD2) return MONT_EINVAL;
+  if (log2R < 2 || log2R > MONT_SWEEP_MAX_LOG2R) return MONT_EINVAL;
+  if (variant >= MONT_PLANTARD && (log2R % 2)) return MONT_EINVAL;
+  if (variant == MONT_SIGNED_PLANTARD2 && (alpha < 0 || alpha > 14)) return MONT_EINVAL;
+  if (N_lo > N_hi || N_hi > MONT_SWEEP_MAX_N || N_hi < 3) return MONT_EINVAL;
+  if (!per_N_counts || !n_cex_total || (cex_cap > 0 && !cex)) return MONT_EINVAL;
+  mont_bounds rules{MONT_DOMAIN_DEFAULT, MONT_RANGE_DEFAULT, 0, 0, 0, 0};
+  if (claimed) rules = *claimed;
+  if (rules.domain_rule < MONT_DOMAIN_DEFAULT || rules.domain_rule > MONT_DOMAIN_EXPLICIT) return MONT_EINVAL;
+  if (rules.range_rule < MONT_RANGE_DEFAULT || rules.range_rule > MONT_RANGE_EXPLICIT) return MONT_EINVAL;
+  const uint32_t first = (N_lo % 2) ? N_lo : N_lo + 1;
+  const size_t n_odd = first > N_hi ? 0 : (N_hi - first) / 2 + 1;
+  // the fixed scratch bounds the request
+  if (n_odd > kNoAllocModuli || cex_cap > kNoAllocCex) return MONT_EINVAL;
+
+  // pass 1: validate every modulus, count the T to sweep
+  uint64_t total_T = 0;
+  for (size_t i = 0; i < n_odd; ++i) {
+    SweepN e;
+    uint64_t checked = 0;
+    const int st = noalloc_entry(variant, log2R, alpha, first + 2 * static_cast<int64_t>(i), flags,
+                                 rules, &e, &checked);
+    if (st != MONT_OK) return st;
+    per_N_counts[i] = 0;
+    if (per_N_checked) per_N_checked[i] = checked;
+    total_T += checked;
+  }
+  *n_cex_total = 0;
+  if (total_T == 0) return MONT_OK;
+
+  char* scratch = nullptr;
+  const int sst = noalloc_scratch(&scratch);
+  if (sst != MONT_OK) return sst;
+  SweepN* d_tab = reinterpret_cast<SweepN*>(scratch);
+  auto* d_counts = reinterpret_cast<unsigned long long*>(scratch + kNoAllocCountsOff);
+  auto* d_cex_n = reinterpret_cast<unsigned long long*>(scratch + kNoAllocCexNOff);
+  auto* d_cex = reinterpret_cast<mont_cex*>(scratch + kNoAllocCexOff);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  uint64_t chunk = 4096;
+  while (chunk > 32 && total_T / chunk < 8 * resident_threads()) chunk >>= 1;
+
+  // pass 2: build the table (every odd N; skipped ones get no chunks) in
+  // small stack blocks; a copy from pageable memory has consumed its source
+  // when cudaMemcpyAsync returns, so the block can be refilled at once
+  constexpr size_t kBlock = 64;
+  SweepN stage[kBlock];
+  uint64_t items = 0;
+  cudaError_t err = cudaSuccess;
+  for (size_t i0 = 0; i0 < n_odd && err == cudaSuccess; i0 += kBlock) {
+    const size_t nb = n_odd - i0 < kBlock ? n_odd - i0 : kBlock;
+    for (size_t j = 0; j < nb; ++j) {
+      uint64_t checked = 0;
+      noalloc_entry(variant, log2R, alpha, first + 2 * static_cast<int64_t>(i0 + j), flags, rules,
+                    &stage[j], &checked);
+      stage[j].item0 = items;
+      items += (checked + chunk - 1) / chunk;
+    }
+    err = cudaMemcpyAsync(d_tab + i0, stage, nb * sizeof(SweepN), cudaMemcpyHostToDevice, s);
+  }
+  // counters start at zero on every call (the array keeps the last call's values)
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_counts, 0, n_odd * sizeof(unsigned long long), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_cex_n, 0, sizeof(unsigned long long), s);
+  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk)};
+  if (err == cudaSuccess) {
+    const int nt = static_cast<int>(n_odd);
+    switch (variant) {
+      case MONT_REDC: err = launch_sweep<MONT_REDC>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
+      case MONT_SIGNED: err = launch_sweep<MONT_SIGNED>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
+      case MONT_PLANTARD: err = launch_sweep<MONT_PLANTARD>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
+      case MONT_SIGNED_PLANTARD: err = launch_sweep<MONT_SIGNED_PLANTARD>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
+      default: err = launch_sweep<MONT_SIGNED_PLANTARD2>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
+    }
+  }
+  unsigned long long h_cex_n = 0;
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(per_N_counts, d_counts, n_odd * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&h_cex_n, d_cex_n, sizeof(h_cex_n), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  size_t n_rec = 0;
+  if (err == cudaSuccess) {
+    n_rec = static_cast<size_t>(h_cex_n < cex_cap ? h_cex_n : cex_cap);
+    if (n_rec) err = cudaMemcpyAsync(cex, d_cex, n_rec * sizeof(mont_cex), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  }
+  if (err != cudaSuccess) return cuda_status(err);
+  uint64_t total = 0;
+  for (size_t i = 0; i < n_odd; ++i) total += per_N_counts[i];
+  std::sort(cex, cex + n_rec, [](const mont_cex& a, const mont_cex& b) {
+    return a.N != b.N ? a.N < b.N : a.T < b.T;
+  });
+  *n_cex_total = static_cast<size_t>(total);
+  return total > cex_cap ? MONT_EOVERFLOW : MONT_OK;
 }
