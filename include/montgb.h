@@ -326,6 +326,79 @@ int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint32_t N_lo, 
                               uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
                               size_t* n_cex_total, void* stream);
 
+/* ------------------------------------------------------------- serving */
+/*
+ * A serving loop for a stream of independent requests (jobs): modular
+ * multiplications (the paper's reductions applied with mont_mul) and
+ * verify sweeps (Section 3's check), batched continuously on one GPU.
+ *
+ * The server owns a device arena of mem_budget_bytes and `slots` worker
+ * threads, each with its own CUDA stream.  Jobs wait in one FIFO queue; the
+ * job at its head is admitted by the next idle worker as soon as its device
+ * buffers fit in the arena (3 * n * element bytes for a modmul job; a
+ * sweep reserves an estimate of its scratch), so requests arriving while
+ * others run start as soon as a slot and memory free up, and up to `slots`
+ * jobs overlap on the device.  A modmul job copies a and b from host memory
+ * into the arena, runs mont_mul and copies the products back into `out`;
+ * pinned host buffers let the copies run asynchronously.  Contexts stay
+ * with the caller (resident across jobs).  A modmul job's wait for the
+ * device is bounded by job_timeout_ms (<= 0: 60 s): a job that exceeds it
+ * completes with MONT_ETIMEOUT and its arena region is retired (never
+ * reused).  A sweep job runs mont_verify_sweep, which synchronises its
+ * stream itself.
+ */
+#define MONT_JOB_MODMUL 0
+#define MONT_JOB_SWEEP  1
+
+typedef struct mont_job {
+  int kind;                    /* MONT_JOB_MODMUL or MONT_JOB_SWEEP                     */
+  /* MODMUL: out[i] = reduce(a[i] b[i]) for ctx; a, b, out HOST pointers of n elements;
+   * ctx and the buffers must stay valid until the job completes.                         */
+  mont_ctx_t ctx;
+  const void* a;
+  const void* b;
+  void* out;
+  size_t n;
+  /* SWEEP: the arguments of mont_verify_sweep; the result buffers must stay valid
+   * until the job completes (claimed is copied at submission).                          */
+  int variant, log2R, alpha;
+  uint32_t N_lo, N_hi;
+  const mont_bounds* claimed;
+  int flags;
+  uint64_t* per_N_counts;
+  uint64_t* per_N_checked;
+  mont_cex* cex;
+  size_t cex_cap;
+  size_t* n_cex_total;
+} mont_job;
+
+typedef struct mont_job_result {
+  int status;        /* the job's status (a sweep's MONT_EOVERFLOW is reported as MONT_OK) */
+  double t_submit;   /* seconds since the server was created                       */
+  double t_admit;    /* admitted to a slot                                        */
+  double t_done;     /* results in host memory                                    */
+} mont_job_result;
+
+typedef struct mont_server* mont_server_t;
+
+/* Create a server on the current device.  MONT_EINVAL for slots outside
+ * 1..64 or a budget below 256 bytes; MONT_ENOMEM if the arena cannot be
+ * allocated. */
+int mont_server_create(mont_server_t* out, size_t mem_budget_bytes, int slots,
+                       int job_timeout_ms);
+/* Queue a job (copied; never blocks on the device) and return its id.
+ * MONT_ENOMEM if the job alone exceeds the budget; MONT_EINVAL on bad fields. */
+int mont_server_submit(mont_server_t server, const mont_job* job, uint64_t* id);
+/* Wait for job `id` (timeout_ms < 0: no limit) and retrieve its result; the
+ * id is then forgotten.  MONT_ETIMEOUT if it is not done in time (it can be
+ * waited for again); MONT_EINVAL for an unknown or already retrieved id. */
+int mont_server_wait(mont_server_t server, uint64_t id, int timeout_ms, mont_job_result* res);
+/* Snapshot: jobs queued, jobs running, free arena bytes, server clock. */
+int mont_server_query(mont_server_t server, size_t* queued, size_t* running,
+                      size_t* arena_free, double* now_s);
+/* Finish every queued job, stop the workers and free the server. */
+int mont_server_destroy(mont_server_t server);
+
 /* ------------------------------------------------------------ autotuner */
 /*
  * Launch shapes.  Every kernel family has a few launch knobs; a per-process
@@ -371,6 +444,18 @@ int mont_autotune(mont_ctx_t ctx, size_t n, int flags, void* stream);
  * (others are ignored).  MONT_EINVAL on I/O or format errors. */
 int mont_tune_save(const char* path);
 int mont_tune_load(const char* path);
+
+/* ----------------------------------------------------------------- probe */
+/*
+ * mont_probe_int_rate -- measured integer throughput of the current GPU for
+ * the instruction mixes of the multi-limb kernels and the sweep: kind 0
+ * mad.lo.u32, 1 mad.hi.u32, 2 mad.lo.cc + madc.hi pairs (counted as two),
+ * 3 add.u32.  A full-occupancy grid runs `iters` iterations of 8 independent
+ * chains per thread; *ops_per_s receives instructions per second (thread
+ * instructions).  Synchronous on `stream`.  Measurement support: the paper
+ * has no counterpart.
+ */
+int mont_probe_int_rate(int kind, int iters, void* stream, double* ops_per_s);
 
 /* ------------------------------------------------------------- utilities */
 /* Static description of a status code; never NULL. */

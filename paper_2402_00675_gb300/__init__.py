@@ -81,6 +81,27 @@ class MontLaunchShape(ctypes.Structure):
                 ("team", ctypes.c_int)]
 
 
+MONT_JOB_MODMUL = 0
+MONT_JOB_SWEEP = 1
+
+
+class MontJob(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ctx", ctypes.c_void_p), ("a", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_size_t),
+                ("variant", ctypes.c_int), ("log2R", ctypes.c_int), ("alpha", ctypes.c_int),
+                ("N_lo", ctypes.c_uint32), ("N_hi", ctypes.c_uint32),
+                ("claimed", ctypes.POINTER(MontBounds)), ("flags", ctypes.c_int),
+                ("per_N_counts", ctypes.POINTER(ctypes.c_uint64)),
+                ("per_N_checked", ctypes.POINTER(ctypes.c_uint64)),
+                ("cex", ctypes.POINTER(MontCex)), ("cex_cap", ctypes.c_size_t),
+                ("n_cex_total", ctypes.POINTER(ctypes.c_size_t))]
+
+
+class MontJobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class MontError(RuntimeError):
     """A non-zero status from the C ABI."""
 
@@ -146,6 +167,13 @@ def _declare(L):
                                              _c.POINTER(MontBounds), _int,
                                              _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64),
                                              _c.POINTER(MontCex), _sz, _c.POINTER(_sz), _vp]),
+        "mont_server_create": (_int, [_c.POINTER(_vp), _sz, _int, _int]),
+        "mont_server_submit": (_int, [_vp, _c.POINTER(MontJob), _c.POINTER(_c.c_uint64)]),
+        "mont_server_wait": (_int, [_vp, _c.c_uint64, _int, _c.POINTER(MontJobResult)]),
+        "mont_server_query": (_int, [_vp, _c.POINTER(_sz), _c.POINTER(_sz), _c.POINTER(_sz),
+                                     _c.POINTER(_c.c_double)]),
+        "mont_server_destroy": (_int, [_vp]),
+        "mont_probe_int_rate": (_int, [_int, _int, _vp, _c.POINTER(_c.c_double)]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -449,6 +477,115 @@ def mont_verify_sweep_noalloc(variant: int, log2R: int, alpha: int, N_lo: int, N
     return SweepResult(moduli, {N: int(counts[i]) for i, N in enumerate(moduli)},
                        {N: int(checked[i]) for i, N in enumerate(moduli)}, ex, total.value,
                        st == MONT_EOVERFLOW)
+
+
+def _host_ptr(x):
+    """Address of host memory: a CPU torch tensor or a numpy array (contiguous)."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor (host pointer argument)")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a contiguous array")
+        return x.ctypes.data
+    raise TypeError(f"cannot take a host pointer of {type(x).__name__}")
+
+
+class Server:
+    """A mont_server_t: continuous batching of modmul and sweep jobs."""
+
+    def __init__(self, mem_budget_bytes: int, slots: int = 4, job_timeout_ms: int = 60000):
+        h = ctypes.c_void_p()
+        _check(lib().mont_server_create(ctypes.byref(h), mem_budget_bytes, slots,
+                                        job_timeout_ms), "mont_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit_modmul(self, ctx: Ctx, a, b, out, n: int | None = None) -> int:
+        """Queue out = a b R^{-1} (host buffers) and return the job id."""
+        if n is None:
+            n = _nbytes(out) // ctx.elem_bytes if hasattr(out, "numel") else out.nbytes // ctx.elem_bytes
+        job = MontJob(kind=MONT_JOB_MODMUL, ctx=ctx.handle, a=_host_ptr(a), b=_host_ptr(b),
+                      out=_host_ptr(out), n=n)
+        jid = ctypes.c_uint64()
+        _check(lib().mont_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)),
+               "mont_server_submit")
+        self._keep[jid.value] = (ctx, a, b, out)
+        return jid.value
+
+    def submit_sweep(self, variant, log2R, alpha, N_lo, N_hi, claimed=None, flags=0,
+                     cex_cap=1024) -> int:
+        first = N_lo if N_lo % 2 else N_lo + 1
+        moduli = list(range(first, N_hi + 1, 2))
+        n = max(len(moduli), 1)
+        counts = (ctypes.c_uint64 * n)()
+        checked = (ctypes.c_uint64 * n)()
+        cex = (MontCex * max(cex_cap, 1))()
+        total = ctypes.c_size_t()
+        job = MontJob(kind=MONT_JOB_SWEEP, variant=variant, log2R=log2R, alpha=alpha, N_lo=N_lo,
+                      N_hi=N_hi, claimed=ctypes.pointer(claimed) if claimed is not None else None,
+                      flags=flags, per_N_counts=counts, per_N_checked=checked, cex=cex,
+                      cex_cap=cex_cap, n_cex_total=ctypes.pointer(total))
+        jid = ctypes.c_uint64()
+        _check(lib().mont_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)),
+               "mont_server_submit")
+        self._keep[jid.value] = (moduli, counts, checked, cex, total, cex_cap)
+        return jid.value
+
+    def wait(self, jid: int, timeout_ms: int = -1) -> dict:
+        """Wait for a job; returns its status and times (plus sweep results)."""
+        res = MontJobResult()
+        _check(lib().mont_server_wait(self.handle, jid, timeout_ms, ctypes.byref(res)),
+               "mont_server_wait")
+        out = {"status": res.status, "t_submit": res.t_submit, "t_admit": res.t_admit,
+               "t_done": res.t_done}
+        keep = self._keep.pop(jid, None)
+        if keep is not None and len(keep) == 6:
+            moduli, counts, checked, cex, total, cap = keep
+            nrec = min(total.value, cap)
+            out["sweep"] = SweepResult(
+                moduli, {N: int(counts[i]) for i, N in enumerate(moduli)},
+                {N: int(checked[i]) for i, N in enumerate(moduli)},
+                [(int(c.N), int(c.T), int(c.r), int(c.expected)) for c in cex[:nrec]],
+                total.value, total.value > cap)
+        return out
+
+    def query(self) -> dict:
+        q, r, f, t = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_double()
+        _check(lib().mont_server_query(self.handle, ctypes.byref(q), ctypes.byref(r),
+                                       ctypes.byref(f), ctypes.byref(t)), "mont_server_query")
+        return {"queued": q.value, "running": r.value, "arena_free": f.value, "now": t.value}
+
+    def close(self):
+        if self.handle:
+            lib().mont_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mont_server_create(mem_budget_bytes: int, slots: int = 4, job_timeout_ms: int = 60000):
+    return Server(mem_budget_bytes, slots, job_timeout_ms)
+
+
+def mont_server_destroy(server: Server) -> None:
+    server.close()
+
+
+def mont_probe_int_rate(kind: int, iters: int = 4096, stream=None) -> float:
+    """Measured thread-instructions per second for an integer mix (see montgb.h)."""
+    r = ctypes.c_double()
+    _check(lib().mont_probe_int_rate(kind, iters, _stream(stream), ctypes.byref(r)),
+           "mont_probe_int_rate")
+    return r.value
 
 
 def mont_sync(stream=None) -> None:

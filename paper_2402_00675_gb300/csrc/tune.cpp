@@ -55,7 +55,17 @@ static void erase_tuned_shape(int width, int variant, int mode) {
   g_table.erase(key);
 }
 
-LaunchShape tuned_batched_shape(int width) { return tuned_shape(width, -1, -1); }
+LaunchShape tuned_batched_shape(int width) {
+  // default when untuned: 256 threads, one 256-bit vector in flight per
+  // operand (measured fastest for the 32-prime RNS batch on GB300)
+  const auto key = std::make_tuple(current_device(), width, -1, -1);
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_table.find(key);
+  if (it != g_table.end()) return it->second;
+  LaunchShape s;
+  s.unroll = 1;
+  return s;
+}
 
 void set_tuned_batched_shape(int width, const LaunchShape& shape) {
   set_tuned_shape(width, -1, -1, shape);
@@ -139,7 +149,8 @@ extern "C" int mont_tune_set(int width_bits, int variant, int mode, const mont_l
 
 extern "C" int mont_tune_get(int width_bits, int variant, int mode, mont_launch_shape* shape) {
   if (!shape || mode < MONT_TUNE_MODE_BATCHED || mode > 3) return MONT_EINVAL;
-  *shape = to_public(tuned_shape(width_bits, mode == MONT_TUNE_MODE_BATCHED ? -1 : variant, mode));
+  *shape = to_public(mode == MONT_TUNE_MODE_BATCHED ? tuned_batched_shape(width_bits)
+                                                    : tuned_shape(width_bits, variant, mode));
   return MONT_OK;
 }
 

@@ -189,3 +189,14 @@ def test_tune_table_set_get_without_gpu(L):
         mg.mont_tune_set(32, 1, 7, {"threads": 128})
     mg.mont_tune_set(32, 1, 0, None)
     assert mg.mont_tune_get(32, 1, 0)["threads"] == 256
+
+
+def test_server_and_device_calls_fail_cleanly_without_gpu(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = L.mont_server_create(ctypes.byref(h), 1 << 20, 2, 0)
+    assert st in (mg.MONT_ECUDA, mg.MONT_ENOMEM)
+    assert L.mont_server_create(ctypes.byref(h), 1 << 20, 0, 0) == mg.MONT_EINVAL
+    assert L.mont_server_destroy(None) == mg.MONT_OK
