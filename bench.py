@@ -62,6 +62,9 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=0, help="0: min(steps, 10)")
     p.add_argument("--cpu-budget-s", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the per-config measurements after the main step")
+    p.add_argument("--serving-jobs", type=int, default=2000)
     p.add_argument("--log2-pairs", type=int, default=26,
                    help="pairs per modulus = 2^this (26 is the benchmark workload)")
     a = p.parse_args()
@@ -171,6 +174,188 @@ def oracle_sample_rate(inputs, budget_s: float):
     total = done * len(MODULI) * len(COMBOS)
     return total / t_used / 1e9, done, t_used
 
+
+
+# ---------------------------------------------------------------- extras
+# Each extra measures one other workload of the library outside the main
+# timed region, with CUDA events on the launching stream, and carries its own
+# roofline.  Peaks: HBM from MEASURED_PEAKS.json; integer peaks derived from
+# unit counts (per SM and clock: 4 schedulers x 32 lanes = 128 issued thread
+# instructions; 64 mad.lo; 32 mad.hi) at the 2070 MHz maximum SM clock.
+
+SMS = 152
+SM_MHZ_MAX = 2070.0
+ISSUE_PEAK = 128 * SMS * SM_MHZ_MAX * 1e6            # thread-instructions / s
+LIMB_PRODUCT_PEAK = 64.0 / 3.0 * SMS * SM_MHZ_MAX * 1e6  # lo + hi product pairs / s
+# integer operations per sweep check of each algorithm's formula (the formula's
+# own operations, the reference step c += s R^-1 mod N, the congruence and
+# range tests and the loop step); see the design doc
+SWEEP_OPS = {0: 16, 1: 17, 2: 16, 3: 17, 4: 16}
+
+
+def _events_ms(fn, reps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_redc32(mg, stream, peak):
+    """REDC, R = 2^32, N = 3329, 2^20 pairs: hot (same buffers, L2-resident)
+    and cold (16 rotating buffer sets, 201 MB > L2)."""
+    import torch
+    N, n = sy.REDC32_N, 1 << 20
+    ctx = mg.mont_ctx_create(N, 32, 0)
+    sets = []
+    for r in range(16):
+        a = torch.from_numpy(sy.uniform_residues(N, n, seed=1 + 100 * r)).cuda()
+        b = torch.from_numpy(sy.uniform_residues(N, n, seed=101 + 100 * r)).cuda()
+        sets.append((a, b, torch.empty_like(a)))
+    L = mg.lib()
+    sp = stream.cuda_stream
+    calls = [(x.data_ptr(), y.data_ptr(), z.data_ptr()) for x, y, z in sets]
+    for _ in range(20):
+        L.mont_mul(ctx.handle, *calls[0], n, sp)
+    hot = _events_ms(lambda: L.mont_mul(ctx.handle, *calls[0], n, sp), 400, stream)
+    k = [0]
+
+    def rot():
+        L.mont_mul(ctx.handle, *calls[k[0] % 16], n, sp)
+        k[0] += 1
+    cold = _events_ms(rot, 400, stream)
+    gb = 12 * n / (cold * 1e-3) / 1e9
+    return {"workload": "REDC R=2^32 N=3329, 2^20 pairs", "unit": "Gmodmul/s",
+            "hot_l2": round(n / (hot * 1e-3) / 1e9, 1), "cold_l2": round(n / (cold * 1e-3) / 1e9, 1),
+            "us_per_launch_hot": round(hot * 1e3, 2), "us_per_launch_cold": round(cold * 1e3, 2),
+            "roofline": {"bound": "hbm", "achieved": round(gb, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gb / peak, 3), "note": "cold-L2 rotation; a 12.6 MB launch "
+                         "is dominated by launch and ramp time"}}
+
+
+def extra_rns64(mg, stream, peak):
+    """32 primes of 60-62 bits, p = 1 mod 2^17, log-uniform lengths 2^12..2^22:
+    one graph-launched persistent batch against 32 plain launches."""
+    import torch
+    primes = sy.rns_primes(32, seed=3)
+    lens = sy.log_uniform_lengths(32, 12, 22, seed=3)
+    ctxs, da, db, outs = [], [], [], []
+    for j, (p_, n) in enumerate(zip(primes, lens)):
+        ctxs.append(mg.mont_ctx_create(p_, 64, 0))
+        da.append(torch.from_numpy(sy.uniform_residues(p_, n, seed=1000 + j, dtype=np.uint64)).cuda())
+        db.append(torch.from_numpy(sy.uniform_residues(p_, n, seed=2000 + j, dtype=np.uint64)).cuda())
+        outs.append(torch.empty(n, dtype=torch.uint64, device="cuda"))
+    plan = mg.Batch(ctxs, da, db, outs, lens)
+    L = mg.lib()
+    sp = stream.cuda_stream
+    calls = [(c.handle, x.data_ptr(), y.data_ptr(), z.data_ptr(), n)
+             for c, x, y, z, n in zip(ctxs, da, db, outs, lens)]
+
+    def plain():
+        for h, x, y, z, n in calls:
+            L.mont_mul(h, x, y, z, n, sp)
+    for _ in range(10):
+        plan.launch(stream)
+        plain()
+    t_batch = _events_ms(lambda: plan.launch(stream), 300, stream)
+    t_plain = _events_ms(plain, 300, stream)
+    tot = sum(lens)
+    gb = 24 * tot / (t_batch * 1e-3) / 1e9
+    plan.close()
+    return {"workload": f"RNS REDC R=2^64, 32 primes, sum(len)={tot}", "unit": "Gmodmul/s",
+            "batched_graph": round(tot / (t_batch * 1e-3) / 1e9, 1),
+            "plain_32_launches": round(tot / (t_plain * 1e-3) / 1e9, 1),
+            "speedup": round(t_plain / t_batch, 2),
+            "us_batched": round(t_batch * 1e3, 2), "us_plain": round(t_plain * 1e3, 2),
+            "roofline": {"bound": "hbm", "achieved": round(gb, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gb / peak, 3)}}
+
+
+def extra_cios(mg, stream, peak):
+    """Multi-limb REDC (CIOS), random odd N of 256/384/1024/2048 bits, operands
+    uniform in [0, N)."""
+    import torch
+    out = {}
+    for bits, count in ((256, 1 << 22), (384, 1 << 21), (1024, 1 << 17), (2048, 1 << 15)):
+        k = bits // 32
+        N = sy.random_odd_modulus(bits, seed=4)
+        ctx = mg.mont_ctx_create(N, bits, 0)
+        a = torch.from_numpy(sy.uniform_limb_residues(N, k, count, seed=40 + k).reshape(-1)).cuda()
+        b = torch.from_numpy(sy.uniform_limb_residues(N, k, count, seed=80 + k).reshape(-1)).cuda()
+        o = torch.empty_like(a)
+        L = mg.lib()
+        sp = stream.cuda_stream
+        f = lambda: L.mont_mul(ctx.handle, a.data_ptr(), b.data_ptr(), o.data_ptr(), count, sp)
+        for _ in range(5):
+            f()
+        ms = _events_ms(f, 50, stream)
+        prods = (2 * k * k + k) * count
+        ach = prods / (ms * 1e-3)
+        gb = 12 * k * count / (ms * 1e-3) / 1e9
+        out[f"{bits}b"] = {
+            "pairs": count, "gmodmul_s": round(count / (ms * 1e-3) / 1e9, 3),
+            "us": round(ms * 1e3, 2), "team": mg.mont_tune_get(bits, 0, 0)["team"] or None,
+            "roofline": {"bound": "alu", "achieved": round(ach / 1e12, 3),
+                         "peak": round(LIMB_PRODUCT_PEAK / 1e12, 3),
+                         "unit": "T limb-products/s (32x32->64, lo+hi)",
+                         "frac": round(ach / LIMB_PRODUCT_PEAK, 3),
+                         "hbm_frac": round(gb / peak, 3)}}
+    return out
+
+
+def extra_sweep(mg, stream):
+    """R = 2^16, every odd N in [3, 4095]; each algorithm on its own domain,
+    and on REDC's domain 0 <= T < RN."""
+    import torch
+    out = {}
+    names = {0: "redc", 1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
+    redc_dom = mg.MontBounds(mg.MONT_DOMAIN_REDC, mg.MONT_RANGE_DEFAULT, 0, 0, 0, 0)
+    for v, alpha in ((0, 0), (1, 0), (2, 0), (3, 0), (4, 1)):
+        for dom_name, dom in (("own_domain", None), ("redc_domain", redc_dom)):
+            mg.mont_verify_sweep(v, 16, alpha, 3, 255, dom, cex_cap=16, stream=stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = mg.mont_verify_sweep(v, 16, alpha, 3, 4095, dom, cex_cap=64, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            checks = sum(r.checked.values())
+            ops = checks * SWEEP_OPS[v]
+            out[f"{names[v]}_{dom_name}"] = {
+                "checks": checks, "counterexamples": r.total,
+                "ms": round(ms, 3), "gchecks_s": round(checks / (ms * 1e-3) / 1e9, 2),
+                "roofline": {"bound": "alu", "achieved": round(ops / (ms * 1e-3) / 1e12, 3),
+                             "peak": round(ISSUE_PEAK / 1e12, 2), "unit": "T int-ops/s",
+                             "frac": round(ops / (ms * 1e-3) / ISSUE_PEAK, 3)}}
+    return out
+
+
+def extra_serving(mg, jobs_count):
+    """Poisson stream of mixed jobs through the serving loop at 0.5x and 0.8x
+    of the measured capacity."""
+    from paper_2402_00675_gb300 import serving
+    ctxs = serving.Contexts.create(3329, sy.rns_primes(1, seed=31)[0],
+                                   sy.random_odd_modulus(256, seed=32))
+    pools = serving.Pools(ctxs, 1 << 24)
+    ring = serving.OutputRing(3 << 30)
+    server = mg.Server(8 << 30, slots=8)
+    out = {"jobs_per_run": jobs_count, "slots": 8, "arena_gb": 8}
+    jobs = sy.serving_jobs(jobs_count, 1.0, seed=5)
+    cap = serving.summarise(serving.run_stream(server, jobs, ctxs, pools, ring, rate_scale=0.0))
+    out["capacity"] = cap
+    for lam in (0.5, 0.8):
+        rate = lam * cap["jobs_per_s"]
+        jobs = sy.serving_jobs(jobs_count, rate, seed=5)
+        out[f"load_{lam}"] = serving.summarise(
+            serving.run_stream(server, jobs, ctxs, pools, ring, rate_scale=1.0))
+    server.close()
+    return out
 
 # ---------------------------------------------------------------- our arm
 
@@ -300,6 +485,16 @@ def run_ours(args):
     peak = peak or 6800.0
     achieved = BYTES_PER_MODMUL * N_PAIRS / (avg_launch_ms * 1e-3) / 1e9
 
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = {
+            "redc32_2p20": extra_redc32(mg, stream, peak),
+            "rns64_batched": extra_rns64(mg, stream, peak),
+            "cios": extra_cios(mg, stream, peak),
+            "sweep_r16": extra_sweep(mg, stream),
+            "serving": extra_serving(mg, args.serving_jobs),
+        }
+
     result = None
     if rank == 0:
         cpu = None
@@ -329,6 +524,7 @@ def run_ours(args):
             "per_variant_gmodmul_s": per_variant,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "extras": extras,
         }
     if world > 1:
         dist.barrier()

@@ -450,7 +450,7 @@ int mont_tune_load(const char* path);
  * mont_probe_int_rate -- measured integer throughput of the current GPU for
  * the instruction mixes of the multi-limb kernels and the sweep: kind 0
  * mad.lo.u32, 1 mad.hi.u32, 2 mad.lo.cc + madc.hi pairs (counted as two),
- * 3 add.u32.  A full-occupancy grid runs `iters` iterations of 8 independent
+ * 3 add.u32, 4 mad.wide.u32 (one 32x32->64 multiply-add).  A full-occupancy grid runs `iters` iterations of 8 independent
  * chains per thread; *ops_per_s receives instructions per second (thread
  * instructions).  Synchronous on `stream`.  Measurement support: the paper
  * has no counterpart.

@@ -7,7 +7,8 @@
 //   kind 0  mad.lo.u32                      (IMAD)
 //   kind 1  mad.hi.u32                      (IMAD.HI)
 //   kind 2  mad.lo.cc / madc.hi.cc pairs    (the carry chains of a CIOS row)
-//   kind 3  add / xor / shift mix           (plain ALU)
+//   kind 3  add.u32                         (plain ALU)
+//   kind 4  mad.wide.u32                    (IMAD.WIDE, a full 32x32->64 product + 64-bit addend)
 // Each thread runs 8 independent accumulators for `iters` iterations; the
 // rate is instructions per second over the whole grid, timed with CUDA events
 // on the caller's stream.  Results go to a file-scope device sink so the work
@@ -36,8 +37,14 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t seed, int iters)
         // two instructions: the low and the high product of one limb
         asm volatile("mad.lo.cc.u32 %0, %0, %1, %0;\n\tmadc.hi.u32 %0, %0, %1, %2;"
                      : "+r"(x[j]) : "r"(m), "r"(c));
-      } else {
+      } else if constexpr (KIND == 3) {
         asm volatile("add.u32 %0, %0, %1;" : "+r"(x[j]) : "r"(c));
+      } else {
+        // both halves feed the chain, so the full 64-bit product is needed
+        asm volatile(
+            "{\n\t.reg .u64 w;\n\t.reg .u32 lo, hi;\n\tmad.wide.u32 w, %0, %1, %2;\n\t"
+            "mov.b64 {lo, hi}, w;\n\txor.b32 %0, lo, hi;\n\t}"
+            : "+r"(x[j]) : "r"(m), "l"(static_cast<uint64_t>(c)));
       }
     }
   }
@@ -61,7 +68,7 @@ cudaError_t launch_rate(cudaStream_t s, int iters, unsigned* grid) {
 using namespace montgb;
 
 extern "C" int mont_probe_int_rate(int kind, int iters, void* stream, double* ops_per_s) {
-  if (kind < 0 || kind > 3 || iters < 1 || !ops_per_s) return MONT_EINVAL;
+  if (kind < 0 || kind > 4 || iters < 1 || !ops_per_s) return MONT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned grid = 0;
   auto launch = [&]() {
@@ -69,7 +76,8 @@ extern "C" int mont_probe_int_rate(int kind, int iters, void* stream, double* op
       case 0: return launch_rate<0>(s, iters, &grid);
       case 1: return launch_rate<1>(s, iters, &grid);
       case 2: return launch_rate<2>(s, iters, &grid);
-      default: return launch_rate<3>(s, iters, &grid);
+      case 3: return launch_rate<3>(s, iters, &grid);
+      default: return launch_rate<4>(s, iters, &grid);
     }
   };
   cudaError_t e = launch();  // warm-up

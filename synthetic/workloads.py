@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "rng", "uniform_residues", "centred_residues", "lift_unsigned", "is_probable_prime",
     "rns_primes", "log_uniform_lengths", "random_odd_modulus", "limbs_of",
-    "int_of_limbs", "uniform_limb_residues", "Job", "serving_jobs",
+    "int_of_limbs", "uniform_limb_residues", "bounded_limb_residues", "Job", "serving_jobs",
     "REDC32_N", "WORD32_MODULI",
 ]
 
@@ -178,6 +178,20 @@ def uniform_limb_residues(N: int, k: int, count: int, seed: int) -> np.ndarray:
     return out
 
 
+def bounded_limb_residues(N: int, k: int, count: int, seed: int) -> np.ndarray:
+    """``count`` residues below N as a (count, k) limb array, drawn fast: the
+    top limb uniform in [0, top limb of N), the others uniform.  Every value is
+    in [0, N), though not uniform over it (used for large serving pools)."""
+    g = rng(seed)
+    n = limbs_of(N, k)
+    out = g.integers(0, 1 << 32, size=(count, k), dtype=np.uint64).astype(np.uint32)
+    top = int(n[k - 1])
+    if top == 0:
+        raise ValueError("N must fill its top limb")
+    out[:, k - 1] = g.integers(0, top, size=count, dtype=np.uint64).astype(np.uint32)
+    return out
+
+
 @dataclass
 class Job:
     """One request of the serving workload."""
@@ -197,7 +211,8 @@ def serving_jobs(count: int, rate_per_s: float, seed: int = 5, sweep_frac: float
     """Poisson stream: exponential inter-arrival times at ``rate_per_s``;
     modmul jobs pick variant from {REDC, signed, Plantard} and width from
     {32, 64, 256} (256-bit is REDC only, so other draws are redrawn); a
-    ``sweep_frac`` share are sweep jobs over ``sweep_moduli`` consecutive odd N."""
+    ``sweep_frac`` share are sweep jobs over ``sweep_moduli`` consecutive odd N
+    at R = 2^16, with the algorithm drawn from {REDC, signed, Plantard}."""
     g = rng(seed)
     t = 0.0
     jobs = []
@@ -206,7 +221,9 @@ def serving_jobs(count: int, rate_per_s: float, seed: int = 5, sweep_frac: float
         if g.uniform() < sweep_frac:
             last_start = sweep_n_max - 2 * (sweep_moduli - 1)
             start = int(g.integers(1, (last_start - 1) // 2 + 1)) * 2 + 1
-            jobs.append(Job(t, "sweep", 0, 16, sweep_moduli, n_lo=start, seed=seed * 1000003 + i))
+            variant = int(g.integers(0, 3))
+            jobs.append(Job(t, "sweep", variant, 16, sweep_moduli, n_lo=start,
+                            seed=seed * 1000003 + i))
             continue
         while True:
             variant = int(g.integers(0, 3))

@@ -69,3 +69,10 @@ def test_serving_jobs_mix():
             assert (1 << 10) <= j.length <= (1 << 24)
         else:
             assert j.n_lo % 2 == 1 and j.n_lo >= 3 and j.n_lo + 2 * 511 <= 4095
+
+
+def test_bounded_limb_residues():
+    N = sy.random_odd_modulus(256, 11)
+    x = sy.bounded_limb_residues(N, 8, 5000, 3)
+    assert x.shape == (5000, 8)
+    assert all(sy.int_of_limbs(r) < N for r in x)
