@@ -47,18 +47,21 @@ template <int V>
 __device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const SweepParams& p) {
   const uint32_t mask = (1u << p.log2R) - 1u;
   const int32_t N = e.N;
+  const int up = 32 - p.log2R;   // sign extension of the low log2R bits: x mods R
   if constexpr (V == MONT_REDC) {
     // m <- (T mod R) N' mod R;  t <- (T + mN) / R;  if t >= N: t - N
-    const uint32_t m = ((static_cast<uint32_t>(T) & mask) * e.nprime) & mask;
+    const uint32_t m = (static_cast<uint32_t>(T) * e.nprime) & mask;
+    if (T >= 0) {
+      // T < 2^31 and m N < 2^16 * 2^15: the sum fits an unsigned word
+      const uint32_t t = (static_cast<uint32_t>(T) + m * static_cast<uint32_t>(N)) >> p.log2R;
+      return static_cast<int32_t>(t >= static_cast<uint32_t>(N) ? t - static_cast<uint32_t>(N) : t);
+    }
     const int64_t t = (static_cast<int64_t>(T) + static_cast<int64_t>(m) * N) >> p.log2R;
     return static_cast<int32_t>(t >= N ? t - N : t);
   } else if constexpr (V == MONT_SIGNED) {
     // T = a1 R + a0;  m0 <- a0 N^{-1} mods R;  t <- floor(m0 N / R);  r <- a1 - t
-    const uint32_t a0 = static_cast<uint32_t>(T) & mask;
     const int32_t a1 = T >> p.log2R;
-    const uint32_t x = (a0 * e.ninv) & mask;
-    const int32_t m0 = x > (mask >> 1) ? static_cast<int32_t>(x) - static_cast<int32_t>(mask) - 1
-                                       : static_cast<int32_t>(x);
+    const int32_t m0 = static_cast<int32_t>((static_cast<uint32_t>(T) * e.ninv) << up) >> up;
     return a1 - ((m0 * N) >> p.log2R);
   } else if constexpr (V == MONT_PLANTARD) {
     // r <- floor((floor((T N^{-1} mod R) / 2^n) + 1) N / 2^n);  if r = N: 0
@@ -66,9 +69,8 @@ __device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const S
     const int32_t r = static_cast<int32_t>((((m >> p.n) + 1u) * static_cast<uint32_t>(N)) >> p.n);
     return r == N ? 0 : r;
   } else {
-    const uint32_t x = (static_cast<uint32_t>(T) * e.ninv) & mask;
-    const int32_t m = x > (mask >> 1) ? static_cast<int32_t>(x) - static_cast<int32_t>(mask) - 1
-                                      : static_cast<int32_t>(x);   // T Ñ^{-1} mods R
+    // m <- T Ñ^{-1} mods R
+    const int32_t m = static_cast<int32_t>((static_cast<uint32_t>(T) * e.ninv) << up) >> up;
     if constexpr (V == MONT_SIGNED_PLANTARD) {
       // r <- round(round(m / 2^n) N / 2^n), halves rounded up
       const int32_t half = 1 << (p.n - 1);
@@ -81,6 +83,46 @@ __device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const S
   }
 }
 
+// r passes when r = c or r = c - N (the only congruent values a default
+// claimed range can hold) and r lies in the claimed range.  Anything else
+// goes through exact_bad.
+__device__ __forceinline__ bool fast_good(int32_t r, uint32_t c, const SweepN& e) {
+  const int32_t ci = static_cast<int32_t>(c);
+  return (r == ci || r == ci - e.N) && r >= e.r_lo && r <= e.r_hi;
+}
+
+// The exact test: counterexample unless r = c (mod N) and r in range.
+__device__ __forceinline__ bool exact_bad(int32_t r, uint32_t c, const SweepN& e) {
+  const int64_t d = static_cast<int64_t>(r) - static_cast<int64_t>(c);
+  const bool cong = (d % static_cast<int64_t>(e.N)) == 0;
+  return !cong || r < e.r_lo || r > e.r_hi;
+}
+
+__device__ __forceinline__ uint32_t add_mod(uint32_t c, uint32_t s, uint32_t N) {
+  const uint32_t x = c + s;            // c, s < N < 2^15
+  return x >= N ? x - N : x;
+}
+
+template <bool kUnsignedTarget>
+__device__ __noinline__ void record(int32_t T, int32_t r, uint32_t c, uint32_t N,
+                                    mont_cex* __restrict__ cex,
+                                    unsigned long long* __restrict__ cex_n,
+                                    unsigned long long cap, bool* full) {
+  if (!*full && *reinterpret_cast<volatile unsigned long long*>(cex_n) >= cap) *full = true;
+  if (*full) return;
+  const unsigned long long slot = atomicAdd(cex_n, 1ull);
+  if (slot >= cap) return;
+  int64_t expect = c;
+  if (!kUnsignedTarget && c > (N - 1u) / 2u) expect -= N;
+  mont_cex rec;
+  rec.N = N;
+  rec.reserved = 0;
+  rec.T = T;
+  rec.r = r;
+  rec.expected = expect;
+  cex[slot] = rec;
+}
+
 template <int V>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ tab, int n_tab,
                                                     uint64_t n_items, SweepParams p,
@@ -90,6 +132,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
                                                     unsigned long long cap) {
   constexpr bool kUnsignedTarget = (V == MONT_REDC || V == MONT_PLANTARD);
   const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  bool full = false;  // the example buffer was seen full: stop touching it
   for (uint64_t item = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; item < n_items;
        item += nthreads) {
     int lo = 0, hi = n_tab - 1;
@@ -104,37 +147,40 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
     const uint32_t N = static_cast<uint32_t>(e.N);
     int64_t tm = T0 % e.N;
     if (tm < 0) tm += e.N;
-    uint32_t c = static_cast<uint32_t>((static_cast<uint64_t>(tm) * e.step) % N);
+    // four reference chains: c_j = s (T0 + j + 4i) R^{-1} mod N
+    const uint32_t s1 = e.step;
+    const uint32_t s2 = add_mod(s1, s1, N), s3 = add_mod(s2, s1, N), s4 = add_mod(s3, s1, N);
+    uint32_t c0 = static_cast<uint32_t>((static_cast<uint64_t>(tm) * e.step) % N);
+    uint32_t c1 = add_mod(c0, s1, N), c2 = add_mod(c0, s2, N), c3 = add_mod(c0, s3, N);
     uint32_t local = 0;
-    bool full = false;  // the example buffer was seen full: stop touching it
     uint32_t Tu = static_cast<uint32_t>(static_cast<int32_t>(T0));
-    for (uint32_t i = 0; i < cnt; ++i, ++Tu) {
+    uint32_t i = 0;
+    for (; i + 4 <= cnt; i += 4, Tu += 4) {
+      const int32_t Ta = static_cast<int32_t>(Tu), Tb = static_cast<int32_t>(Tu + 1u);
+      const int32_t Tc = static_cast<int32_t>(Tu + 2u), Td = static_cast<int32_t>(Tu + 3u);
+      const int32_t ra = candidate<V>(Ta, e, p), rb = candidate<V>(Tb, e, p);
+      const int32_t rc = candidate<V>(Tc, e, p), rd = candidate<V>(Td, e, p);
+      const bool ga = fast_good(ra, c0, e), gb = fast_good(rb, c1, e);
+      const bool gc = fast_good(rc, c2, e), gd = fast_good(rd, c3, e);
+      if (!(ga && gb && gc && gd)) {
+        if (!ga && exact_bad(ra, c0, e)) { ++local; record<kUnsignedTarget>(Ta, ra, c0, N, cex, cex_n, cap, &full); }
+        if (!gb && exact_bad(rb, c1, e)) { ++local; record<kUnsignedTarget>(Tb, rb, c1, N, cex, cex_n, cap, &full); }
+        if (!gc && exact_bad(rc, c2, e)) { ++local; record<kUnsignedTarget>(Tc, rc, c2, N, cex, cex_n, cap, &full); }
+        if (!gd && exact_bad(rd, c3, e)) { ++local; record<kUnsignedTarget>(Td, rd, c3, N, cex, cex_n, cap, &full); }
+      }
+      c0 = add_mod(c0, s4, N);
+      c1 = add_mod(c1, s4, N);
+      c2 = add_mod(c2, s4, N);
+      c3 = add_mod(c3, s4, N);
+    }
+    for (; i < cnt; ++i, ++Tu) {
       const int32_t T = static_cast<int32_t>(Tu);
       const int32_t r = candidate<V>(T, e, p);
-      const int64_t d = static_cast<int64_t>(r) - static_cast<int64_t>(c);
-      const bool cong = d == 0 || d == -static_cast<int64_t>(N) || d == static_cast<int64_t>(N) ||
-                        (d % static_cast<int64_t>(N)) == 0;
-      const bool bad = !cong || r < e.r_lo || r > e.r_hi;
-      if (bad) {
+      if (!fast_good(r, c0, e) && exact_bad(r, c0, e)) {
         ++local;
-        if (!full && *reinterpret_cast<volatile unsigned long long*>(cex_n) >= cap) full = true;
-        if (!full) {
-          const unsigned long long slot = atomicAdd(cex_n, 1ull);
-          if (slot < cap) {
-            int64_t expect = c;
-            if (!kUnsignedTarget && c > (N - 1u) / 2u) expect -= N;
-            mont_cex rec;
-            rec.N = N;
-            rec.reserved = 0;
-            rec.T = T;
-            rec.r = r;
-            rec.expected = expect;
-            cex[slot] = rec;
-          }
-        }
+        record<kUnsignedTarget>(T, r, c0, N, cex, cex_n, cap, &full);
       }
-      c += e.step;
-      if (c >= N) c -= N;
+      c0 = add_mod(c0, s1, N);
     }
     if (local) atomicAdd(counts + lo, static_cast<unsigned long long>(local));
   }

@@ -133,3 +133,13 @@ def test_full_sweep_redc_domain_for_every_variant():
                 continue
             want = o.sweep(variant, 16, alpha, N, N, domain=ex.DOMAIN_REDC, vectorised=True)
             assert got.counts[N] == want.counts[N], (variant, N)
+
+
+def test_redc_sweep_r16_moduli_to_1023():
+    """REDC at R = 2^16 over every odd N <= 1023 (1.7e10 checks): no
+    counterexample, full domains checked, oracle agreement on sampled N."""
+    got = mg.mont_verify_sweep(mg.MONT_REDC, 16, 0, 3, 1023, cex_cap=64)
+    assert got.total == 0
+    assert all(got.checked[N] == (1 << 16) * N for N in got.moduli)
+    for N in (3, 255, 1023):
+        assert o.sweep(o.REDC, 16, 0, N, N, vectorised=True).counts[N] == got.counts[N] == 0
