@@ -80,6 +80,24 @@ def dist_env():
     return rank, world, local
 
 
+# ---------------------------------------------------------------- ranks
+
+def max_over_ranks(elapsed_ms: float, world: int, device: str = "cuda") -> float:
+    """The job's time: the largest of the ranks' times (all ranks call this)."""
+    if world == 1:
+        return elapsed_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, elapsed_ms: float) -> float:
+    """Units of every rank (each rank runs the same replica) per second, in 1e9."""
+    return world * units_per_rank / (elapsed_ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- inputs
 
 def make_inputs():
@@ -422,11 +440,7 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
 
     per_launch = [[evs[k][j][0].elapsed_time(evs[k][j][1]) for k in range(K)]
                   for j in range(len(calls))]
@@ -438,7 +452,7 @@ def run_ours(args):
         per_variant[f"{VARIANT_NAMES[variant]}_N{N}"] = round(N_PAIRS / (ms * 1e-3) / 1e9, 2)
 
     modmuls_per_step = N_PAIRS * len(calls)
-    value = world * modmuls_per_step * K / (elapsed_ms * 1e-3) / 1e9
+    value = whole_job_rate(modmuls_per_step * K, world, elapsed_ms)
 
     # ---------------- end to end: pinned host operands in, products out
     e2e_steps = args.e2e_steps or min(K, 10)
@@ -466,12 +480,8 @@ def run_ours(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * modmuls_per_step * e2e_steps / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = whole_job_rate(modmuls_per_step * e2e_steps, world, e2e_ms)
 
     # ---------------- roofline of the dominant kernel (the word kernel)
     peaks = {}
