@@ -47,10 +47,12 @@ VARIANT_NAMES = {1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
 BYTES_PER_MODMUL = 12          # two 4-byte operands in, one 4-byte product out
 ALPHA = 1
 
-# DRAM bytes per launch of the word kernel on this workload, from one ncu
-# capture of the same launch (profiles/word32_mont_mul_2p26.md); None until
-# a capture of the current kernel exists.
-NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes per launch of the word kernel on this workload (read + write,
+# mean of the 8 launches of one step), from a one-pass ncu capture of the
+# full-size launch (profiles/word32_mont_mul_2p26.md).  Reads equal the
+# algorithmic 536.9 MB; writes (228.1 MB of 268.4 MB) exclude the output tail
+# still dirty in L2 when the kernel ends, which the next launch writes back.
+NCU_TRAFFIC_BYTES_PER_LAUNCH = 764974976
 
 
 def parse_args():
@@ -461,13 +463,49 @@ def run_ours(args):
     h2d = sum(t.numel() * t.element_size() for N in MODULI for t in host_in[N])
     d2h = sum(t.numel() * t.element_size() for t in host_out.values())
 
+    # The e2e step is pipelined over chunks of E2E_CHUNK elements on three
+    # streams: the host-to-device copies of chunk c+1 overlap the products of
+    # chunk c and the device-to-host copies of chunk c-1 (the link carries
+    # both directions at once).  Every chunk runs the same 8 mont_mul calls as
+    # the device-resident step, on slices of the same device arrays.
+    E2E_CHUNK = 1 << 22
+    s_in = torch.cuda.Stream()
+    s_out = torch.cuda.Stream()
+    n_chunks = (N_PAIRS + E2E_CHUNK - 1) // E2E_CHUNK
+    keys = list(outs.keys())
+    elem = 4
+
     def e2e_step():
-        for N in MODULI:
-            for d, h in zip(dev_in[N], host_in[N]):
-                d.copy_(h, non_blocking=True)
-        step()
-        for key, h in host_out.items():
-            h.copy_(outs[key], non_blocking=True)
+        start_ev = torch.cuda.Event()
+        start_ev.record(stream)
+        s_in.wait_event(start_ev)
+        s_out.wait_event(start_ev)
+        for c in range(n_chunks):
+            lo = c * E2E_CHUNK
+            hi = min(N_PAIRS, lo + E2E_CHUNK)
+            with torch.cuda.stream(s_in):
+                for N in MODULI:
+                    for d, h in zip(dev_in[N], host_in[N]):
+                        d[lo:hi].copy_(h[lo:hi], non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+            stream.wait_event(ev_in)
+            for (key, hnd, xp, yp, op) in calls:
+                st = L.mont_mul(hnd, xp + lo * elem, yp + lo * elem, op + lo * elem, hi - lo, sptr)
+                if st:
+                    raise mg.MontError(st, "mont_mul")
+            ev_c = torch.cuda.Event()
+            ev_c.record(stream)
+            s_out.wait_event(ev_c)
+            with torch.cuda.stream(s_out):
+                for key in keys:
+                    host_out[key][lo:hi].copy_(outs[key][lo:hi], non_blocking=True)
+        end_in = torch.cuda.Event()
+        end_in.record(s_in)
+        end_out = torch.cuda.Event()
+        end_out.record(s_out)
+        stream.wait_event(end_in)
+        stream.wait_event(end_out)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -480,6 +518,13 @@ def run_ours(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    # the results arrived: check a sample of every output against the
+    # device-resident step's products
+    for key in keys:
+        idx = torch.randint(0, N_PAIRS, (4096,))
+        h = host_out[key].view(torch.int32)
+        d = outs[key].view(torch.int32)
+        assert torch.equal(h[idx], d[idx.cuda()].cpu()), key
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = whole_job_rate(modmuls_per_step * e2e_steps, world, e2e_ms)
 
