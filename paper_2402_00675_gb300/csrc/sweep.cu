@@ -41,6 +41,7 @@ struct SweepParams {
   int n;            // log2R / 2 (Plantard family)
   int alpha;
   uint32_t chunk;   // T per chunk
+  int range_kind;   // RangeKind of the claimed range
 };
 
 template <int V>
@@ -83,17 +84,30 @@ __device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const S
   }
 }
 
-// r passes when r = c or r = c - N (the only congruent values a default
-// claimed range can hold) and r lies in the claimed range.  Anything else
-// goes through exact_bad.
+// How the claimed range is tested.  The reference c = s T R^{-1} mod N is
+// kept in [0, N) (kept centred in [-(N-1)/2, (N-1)/2] for kCentred), and:
+//   kUnsigned  range [0, N-1]:            the only congruent value in range is c
+//   kCentred   range [-(N-1)/2, (N-1)/2]: the only congruent value in range is c
+//   kWide      range [-(N-1), N-1]:       c, and c - N when c != 0
+//   kGeneric   any explicit range:        c or c - N inside the range
+// A check that fails these goes through exact_bad, so the verdict is exact.
+enum RangeKind : int { kUnsigned = 0, kCentred = 1, kWide = 2, kGeneric = 3 };
+
+template <int RK>
 __device__ __forceinline__ bool fast_good(int32_t r, uint32_t c, const SweepN& e) {
   const int32_t ci = static_cast<int32_t>(c);
-  return (r == ci || r == ci - e.N) && r >= e.r_lo && r <= e.r_hi;
+  if constexpr (RK == kUnsigned || RK == kCentred) {
+    return r == ci;
+  } else if constexpr (RK == kWide) {
+    return r == ci || (r == ci - e.N && ci != 0);
+  } else {
+    return (r == ci || r == ci - e.N) && r >= e.r_lo && r <= e.r_hi;
+  }
 }
 
 // The exact test: counterexample unless r = c (mod N) and r in range.
 __device__ __forceinline__ bool exact_bad(int32_t r, uint32_t c, const SweepN& e) {
-  const int64_t d = static_cast<int64_t>(r) - static_cast<int64_t>(c);
+  const int64_t d = static_cast<int64_t>(r) - static_cast<int64_t>(static_cast<int32_t>(c));
   const bool cong = (d % static_cast<int64_t>(e.N)) == 0;
   return !cong || r < e.r_lo || r > e.r_hi;
 }
@@ -101,6 +115,19 @@ __device__ __forceinline__ bool exact_bad(int32_t r, uint32_t c, const SweepN& e
 __device__ __forceinline__ uint32_t add_mod(uint32_t c, uint32_t s, uint32_t N) {
   const uint32_t x = c + s;            // c, s < N < 2^15
   return x >= N ? x - N : x;
+}
+
+// c + s for a centred c in [-(N-1)/2, (N-1)/2] and 0 <= s < N, kept centred.
+__device__ __forceinline__ uint32_t add_mod_centred(uint32_t c, uint32_t s, uint32_t N) {
+  const int32_t x = static_cast<int32_t>(c) + static_cast<int32_t>(s);
+  const int32_t h = static_cast<int32_t>((N - 1u) / 2u);
+  return static_cast<uint32_t>(x > h ? x - static_cast<int32_t>(N) : x);
+}
+
+template <int RK>
+__device__ __forceinline__ uint32_t step_ref(uint32_t c, uint32_t s, uint32_t N) {
+  if constexpr (RK == kCentred) return add_mod_centred(c, s, N);
+  else return add_mod(c, s, N);
 }
 
 template <bool kUnsignedTarget>
@@ -112,8 +139,10 @@ __device__ __noinline__ void record(int32_t T, int32_t r, uint32_t c, uint32_t N
   if (*full) return;
   const unsigned long long slot = atomicAdd(cex_n, 1ull);
   if (slot >= cap) return;
-  int64_t expect = c;
-  if (!kUnsignedTarget && c > (N - 1u) / 2u) expect -= N;
+  // c is in [0, N) or, for a centred chain, already in [-(N-1)/2, (N-1)/2]
+  int64_t expect = static_cast<int32_t>(c);
+  if (expect < 0) expect += N;
+  if (!kUnsignedTarget && expect > static_cast<int64_t>((N - 1u) / 2u)) expect -= N;
   mont_cex rec;
   rec.N = N;
   rec.reserved = 0;
@@ -123,7 +152,7 @@ __device__ __noinline__ void record(int32_t T, int32_t r, uint32_t c, uint32_t N
   cex[slot] = rec;
 }
 
-template <int V>
+template <int V, int RK>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ tab, int n_tab,
                                                     uint64_t n_items, SweepParams p,
                                                     unsigned long long* __restrict__ counts,
@@ -152,6 +181,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
     const uint32_t s2 = add_mod(s1, s1, N), s3 = add_mod(s2, s1, N), s4 = add_mod(s3, s1, N);
     uint32_t c0 = static_cast<uint32_t>((static_cast<uint64_t>(tm) * e.step) % N);
     uint32_t c1 = add_mod(c0, s1, N), c2 = add_mod(c0, s2, N), c3 = add_mod(c0, s3, N);
+    if constexpr (RK == kCentred) {  // move the chains to the centred representatives
+      const uint32_t h = (N - 1u) / 2u;
+      c0 = c0 > h ? c0 - N : c0;
+      c1 = c1 > h ? c1 - N : c1;
+      c2 = c2 > h ? c2 - N : c2;
+      c3 = c3 > h ? c3 - N : c3;
+    }
     uint32_t local = 0;
     uint32_t Tu = static_cast<uint32_t>(static_cast<int32_t>(T0));
     uint32_t i = 0;
@@ -160,27 +196,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
       const int32_t Tc = static_cast<int32_t>(Tu + 2u), Td = static_cast<int32_t>(Tu + 3u);
       const int32_t ra = candidate<V>(Ta, e, p), rb = candidate<V>(Tb, e, p);
       const int32_t rc = candidate<V>(Tc, e, p), rd = candidate<V>(Td, e, p);
-      const bool ga = fast_good(ra, c0, e), gb = fast_good(rb, c1, e);
-      const bool gc = fast_good(rc, c2, e), gd = fast_good(rd, c3, e);
+      const bool ga = fast_good<RK>(ra, c0, e), gb = fast_good<RK>(rb, c1, e);
+      const bool gc = fast_good<RK>(rc, c2, e), gd = fast_good<RK>(rd, c3, e);
       if (!(ga && gb && gc && gd)) {
         if (!ga && exact_bad(ra, c0, e)) { ++local; record<kUnsignedTarget>(Ta, ra, c0, N, cex, cex_n, cap, &full); }
         if (!gb && exact_bad(rb, c1, e)) { ++local; record<kUnsignedTarget>(Tb, rb, c1, N, cex, cex_n, cap, &full); }
         if (!gc && exact_bad(rc, c2, e)) { ++local; record<kUnsignedTarget>(Tc, rc, c2, N, cex, cex_n, cap, &full); }
         if (!gd && exact_bad(rd, c3, e)) { ++local; record<kUnsignedTarget>(Td, rd, c3, N, cex, cex_n, cap, &full); }
       }
-      c0 = add_mod(c0, s4, N);
-      c1 = add_mod(c1, s4, N);
-      c2 = add_mod(c2, s4, N);
-      c3 = add_mod(c3, s4, N);
+      c0 = step_ref<RK>(c0, s4, N);
+      c1 = step_ref<RK>(c1, s4, N);
+      c2 = step_ref<RK>(c2, s4, N);
+      c3 = step_ref<RK>(c3, s4, N);
     }
     for (; i < cnt; ++i, ++Tu) {
       const int32_t T = static_cast<int32_t>(Tu);
       const int32_t r = candidate<V>(T, e, p);
-      if (!fast_good(r, c0, e) && exact_bad(r, c0, e)) {
+      if (!fast_good<RK>(r, c0, e) && exact_bad(r, c0, e)) {
         ++local;
         record<kUnsignedTarget>(T, r, c0, N, cex, cex_n, cap, &full);
       }
-      c0 = add_mod(c0, s1, N);
+      c0 = step_ref<RK>(c0, s1, N);
     }
     if (local) atomicAdd(counts + lo, static_cast<unsigned long long>(local));
   }
@@ -242,17 +278,43 @@ void default_range(int variant, int64_t N, int64_t* lo, int64_t* hi) {
   }
 }
 
+template <int V, int RK>
+cudaError_t launch_sweep_rk(const SweepN* tab, int n_tab, uint64_t n_items, const SweepParams& p,
+                            unsigned long long* counts, mont_cex* cex, unsigned long long* cex_n,
+                            unsigned long long cap, cudaStream_t s) {
+  const int threads = 256;
+  const int per_sm = resident_blocks(reinterpret_cast<const void*>(sweep_kernel<V, RK>), threads);
+  const uint64_t cap_blocks = static_cast<uint64_t>(device_sm_count()) * per_sm;
+  const uint64_t want = (n_items + threads - 1) / threads;
+  const unsigned grid = static_cast<unsigned>(want < cap_blocks ? want : cap_blocks);
+  sweep_kernel<V, RK><<<grid, threads, 0, s>>>(tab, n_tab, n_items, p, counts, cex, cex_n, cap);
+  return cudaGetLastError();
+}
+
+// The range kind of a call: the claimed range rule resolved for the variant.
+int range_kind(int variant, int range_rule) {
+  switch (range_rule) {
+    case MONT_RANGE_UNSIGNED: return kUnsigned;
+    case MONT_RANGE_WIDE: return kWide;
+    case MONT_RANGE_CENTRED: return kCentred;
+    case MONT_RANGE_DEFAULT:
+      if (variant == MONT_REDC || variant == MONT_PLANTARD) return kUnsigned;
+      if (variant == MONT_SIGNED) return kWide;
+      return kCentred;
+  }
+  return kGeneric;
+}
+
 template <int V>
 cudaError_t launch_sweep(const SweepN* tab, int n_tab, uint64_t n_items, const SweepParams& p,
                          unsigned long long* counts, mont_cex* cex, unsigned long long* cex_n,
                          unsigned long long cap, cudaStream_t s) {
-  const int threads = 256;
-  const int per_sm = resident_blocks(reinterpret_cast<const void*>(sweep_kernel<V>), threads);
-  const uint64_t cap_blocks = static_cast<uint64_t>(device_sm_count()) * per_sm;
-  const uint64_t want = (n_items + threads - 1) / threads;
-  const unsigned grid = static_cast<unsigned>(want < cap_blocks ? want : cap_blocks);
-  sweep_kernel<V><<<grid, threads, 0, s>>>(tab, n_tab, n_items, p, counts, cex, cex_n, cap);
-  return cudaGetLastError();
+  switch (p.range_kind) {
+    case kUnsigned: return launch_sweep_rk<V, kUnsigned>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
+    case kCentred: return launch_sweep_rk<V, kCentred>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
+    case kWide: return launch_sweep_rk<V, kWide>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
+    default: return launch_sweep_rk<V, kGeneric>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
+  }
 }
 
 }  // namespace
@@ -338,7 +400,8 @@ extern "C" int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_l
     e.item0 = items;
     items += (static_cast<uint64_t>(e.t_hi - e.t_lo) + chunk) / chunk;
   }
-  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk)};
+  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk),
+                range_kind(variant, rules.range_rule)};
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t n_tab = tab.size();
@@ -563,7 +626,8 @@ extern "C" int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint
   // counters start at zero on every call (the array keeps the last call's values)
   if (err == cudaSuccess) err = cudaMemsetAsync(d_counts, 0, n_odd * sizeof(unsigned long long), s);
   if (err == cudaSuccess) err = cudaMemsetAsync(d_cex_n, 0, sizeof(unsigned long long), s);
-  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk)};
+  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk),
+                range_kind(variant, rules.range_rule)};
   if (err == cudaSuccess) {
     const int nt = static_cast<int>(n_odd);
     switch (variant) {
