@@ -170,6 +170,59 @@ int mont_to_domain(mont_ctx_t ctx, const void* x, void* out, size_t n, void* str
  */
 int mont_from_domain(mont_ctx_t ctx, const void* y, void* out, size_t n, void* stream);
 
+/* -------------------------------------------- fixed multipliers (Plantard) */
+/*
+ * Section 3.2: Plantard's reduction lets a fixed multiplier b be prepared once
+ * as b' = b N^{-1} mod R (R = 2^{2n}); the reduction of a b then needs only
+ * m = a b' mod R, a word-by-double-word low product of which one word is
+ * used, instead of T = a b and T N^{-1} mod R.  Plantard-family contexts at
+ * word widths only (MONT_EINVAL otherwise).
+ *
+ * mont_const_prepare -- b_pre[i] = b[i] N^{-1} mod R.  b: device array of n
+ *   ctx elements in the variant's input range; b_pre: device array of n double
+ *   words (uint64_t at 32 bits; two little-endian uint64_t at 64 bits),
+ *   aligned to its double-word size.  Asynchronous.
+ * mont_mul_pre -- out[i] = the variant's reduction of a[i] b[i], using b_pre:
+ *   bit-identical to mont_mul(a, b).  out may alias a exactly; b_pre must not
+ *   overlap a or out.  Asynchronous.
+ */
+int mont_const_prepare(mont_ctx_t ctx, const void* b, void* b_pre, size_t n, void* stream);
+int mont_mul_pre(mont_ctx_t ctx, const void* a, const void* b_pre, void* out, size_t n,
+                 void* stream);
+
+/* ------------------------------------------------------------------ NTT */
+/*
+ * Batched negacyclic number-theoretic transform over Z_N, the application the
+ * paper gives for word-size Montgomery-type reductions (Section 1); each
+ * butterfly's twiddle product is a REDC product with the twiddle in
+ * Montgomery form, or a Plantard product with the twiddle in the prepared
+ * form of Section 3.2, so the data stays in the plain representation.
+ *
+ *   forward: A[i] = sum_j a[j] psi^{(2 brv(i) + 1) j} mod N   (bit-reversed output)
+ *   inverse: a[j] = n^{-1} sum_i A[i] psi^{-(2 brv(i) + 1) j} mod N
+ *
+ * with n = 2^log2n, brv the log2n-bit reversal and psi a primitive 2n-th root
+ * of unity mod N (psi^n = -1 mod N).
+ *
+ * mont_ntt_create -- plan for ctx (MONT_REDC or MONT_PLANTARD, 32- or 64-bit
+ *   words), 5 <= log2n <= 10, psi as ctx->n_limbs little-endian 32-bit limbs.
+ *   Builds the twiddle tables on the host and copies them to a device
+ *   allocation owned by the plan (synchronous).  MONT_EINVAL when psi^n != -1
+ *   mod N or the parameters are unsupported.  The plan copies the ctx's
+ *   constants; the ctx may be destroyed afterwards.
+ * mont_ntt_forward / mont_ntt_inverse -- transform `batch` polynomials of n
+ *   coefficients in [0, N), stored one after another (polynomial p occupies
+ *   elements [p n, (p+1) n)); device pointers; in == out allowed (in place),
+ *   partial overlap refused.  Asynchronous on `stream`.
+ * mont_ntt_destroy -- free the plan (NULL accepted); work already enqueued
+ *   must have completed.
+ */
+typedef struct mont_ntt* mont_ntt_t;
+int mont_ntt_create(mont_ntt_t* out, mont_ctx_t ctx, int log2n, const uint32_t* psi_limbs);
+int mont_ntt_forward(mont_ntt_t plan, const void* in, void* out, size_t batch, void* stream);
+int mont_ntt_inverse(mont_ntt_t plan, const void* in, void* out, size_t batch, void* stream);
+int mont_ntt_destroy(mont_ntt_t plan);
+
 /* ---------------------------------------------------------- batched RNS */
 /*
  * mont_mul_batched -- many independent mont_mul problems in one persistent

@@ -174,6 +174,12 @@ def _declare(L):
                                      _c.POINTER(_c.c_double)]),
         "mont_server_destroy": (_int, [_vp]),
         "mont_probe_int_rate": (_int, [_int, _int, _vp, _c.POINTER(_c.c_double)]),
+        "mont_const_prepare": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_mul_pre": (_int, [_vp, _vp, _vp, _vp, _sz, _vp]),
+        "mont_ntt_create": (_int, [_c.POINTER(_vp), _vp, _int, _u32p]),
+        "mont_ntt_forward": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_ntt_inverse": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_ntt_destroy": (_int, [_vp]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -586,6 +592,58 @@ def mont_probe_int_rate(kind: int, iters: int = 4096, stream=None) -> float:
     _check(lib().mont_probe_int_rate(kind, iters, _stream(stream), ctypes.byref(r)),
            "mont_probe_int_rate")
     return r.value
+
+
+def mont_const_prepare(ctx: Ctx, b, b_pre, n: int | None = None, stream=None) -> None:
+    """b_pre[i] = b[i] N^{-1} mod R (Plantard family; see montgb.h)."""
+    _check(lib().mont_const_prepare(ctx, _ptr(b), _ptr(b_pre), _count(ctx, b, n),
+                                    _stream(stream)), "mont_const_prepare")
+
+
+def mont_mul_pre(ctx: Ctx, a, b_pre, out, n: int | None = None, stream=None) -> None:
+    """out[i] = reduce(a[i] b[i]) from the prepared multipliers b_pre."""
+    _check(lib().mont_mul_pre(ctx, _ptr(a), _ptr(b_pre), _ptr(out), _count(ctx, out, n),
+                              _stream(stream)), "mont_mul_pre")
+
+
+class Ntt:
+    """A mont_ntt_t plan: batched negacyclic NTTs of length 2^log2n."""
+
+    def __init__(self, ctx: Ctx, log2n: int, psi: int):
+        h = ctypes.c_void_p()
+        _check(lib().mont_ntt_create(ctypes.byref(h), ctx, log2n, _limbs(psi, ctx.n_limbs)),
+               "mont_ntt_create")
+        self.handle = h.value
+        self.n = 1 << log2n
+        self.elem_bytes = ctx.elem_bytes
+
+    def _batch(self, x, batch):
+        if batch is not None:
+            return int(batch)
+        return _nbytes(x) // (self.elem_bytes * self.n)
+
+    def forward(self, x, out, batch: int | None = None, stream=None) -> None:
+        _check(lib().mont_ntt_forward(self.handle, _ptr(x), _ptr(out), self._batch(x, batch),
+                                      _stream(stream)), "mont_ntt_forward")
+
+    def inverse(self, x, out, batch: int | None = None, stream=None) -> None:
+        _check(lib().mont_ntt_inverse(self.handle, _ptr(x), _ptr(out), self._batch(x, batch),
+                                      _stream(stream)), "mont_ntt_inverse")
+
+    def close(self):
+        if self.handle:
+            lib().mont_ntt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mont_ntt_create(ctx: Ctx, log2n: int, psi: int) -> Ntt:
+    return Ntt(ctx, log2n, psi)
 
 
 def mont_sync(stream=None) -> None:

@@ -1,0 +1,522 @@
+// Batched negacyclic number-theoretic transform (mont_ntt_*).
+//
+// The paper names the NTT of lattice and homomorphic-encryption schemes as
+// the reason word-size Montgomery-type reductions matter (Section 1) and
+// Plantard's fixed-multiplier form as what makes his reduction attractive
+// there (Section 3.2); the transform itself is textbook:
+//   forward  A[i] = sum_j a[j] psi^{(2 brv(i) + 1) j}  (mod N), bit-reversed output,
+//   inverse  a[j] = n^{-1} sum_i A[i] psi^{-(2 brv(i) + 1) j},
+// for a primitive 2n-th root of unity psi.  Forward layers are Cooley-Tukey
+// butterflies (x, y) -> (x + w y, x - w y) with w = psi^{brv(k)}, k = n/(2 len)
+// + group, for len = n/2 down to 1; the inverse undoes them in reverse order,
+// (X, Y) -> (X + Y, (X - Y) w^{-1}), and scales by n^{-1} at the end.
+//
+// Mapping: one warp owns one polynomial; lane t holds the n/32 coefficients
+// t + 32 e in registers.  Layers with len >= 32 pair registers of one lane;
+// the five layers with len < 32 pair lane t with lane t ^ len through one
+// shuffle, both lanes computing the same product w y.  Twiddles live in
+// shared memory in multiplier form: w R mod N for REDC (so REDC(y * wR) =
+// y w), and Plantard's prepared b' = (-w R mod N) N^{-1} mod R for the
+// Plantard reduction (so the product -y (-wR) R^{-1} = y w); the data stays
+// in the plain representation [0, N).
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "word_kernel.cuh"
+
+namespace montgb {
+namespace {
+
+template <class Op>
+struct Tw;
+template <>
+struct Tw<Redc32> {
+  using T = uint32_t;
+  static __device__ __forceinline__ uint32_t mul(uint32_t y, T w, const WordConst32& c) {
+    return Redc32::reduce(Redc32::mul(y, w), c);
+  }
+};
+template <>
+struct Tw<Plantard32> {
+  using T = uint64_t;
+  static __device__ __forceinline__ uint32_t mul(uint32_t y, T w, const WordConst32& c) {
+    return Plantard32::mul_pre(y, w, c);
+  }
+};
+template <>
+struct Tw<Redc64> {
+  using T = uint64_t;
+  static __device__ __forceinline__ uint64_t mul(uint64_t y, T w, const WordConst64& c) {
+    return Redc64::reduce(Redc64::mul(y, w), c);
+  }
+};
+template <>
+struct Tw<Plantard64> {
+  using T = u128;
+  static __device__ __forceinline__ uint64_t mul(uint64_t y, T w, const WordConst64& c) {
+    return Plantard64::mul_pre(y, w, c);
+  }
+};
+
+template <class E>
+__device__ __forceinline__ E add_n(E x, E t, E N) {  // x, t in [0, N)
+  const E s = x + t;
+  return (s < x || s >= N) ? s - N : s;
+}
+template <class E>
+__device__ __forceinline__ E sub_n(E x, E t, E N) {
+  return x >= t ? x - t : x - t + N;
+}
+
+template <class Op, int LOG2N, int L, bool INV>
+__device__ __forceinline__ void layer(typename Op::E (&v)[(1 << LOG2N) / 32],
+                                      const typename Tw<Op>::T* stw, int lane,
+                                      const typename Op::C& c) {
+  using E = typename Op::E;
+  constexpr int n = 1 << LOG2N;
+  constexpr int EPT = n / 32;
+  constexpr int len = 1 << L;
+  const E N = static_cast<E>(c.N);
+  if constexpr (len >= 32) {
+    constexpr int h = len / 32;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      if ((e & h) == 0) {
+        const int k = (n >> (L + 1)) + (e >> (L - 4));
+        const typename Tw<Op>::T w = stw[k];
+        const E x = v[e], y = v[e + h];
+        if constexpr (!INV) {
+          const E t = Tw<Op>::mul(y, w, c);
+          v[e] = add_n<E>(x, t, N);
+          v[e + h] = sub_n<E>(x, t, N);
+        } else {
+          v[e] = add_n<E>(x, y, N);
+          v[e + h] = Tw<Op>::mul(sub_n<E>(x, y, N), w, c);
+        }
+      }
+    }
+  } else {
+    const bool upper = (lane & len) != 0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int k = (n >> (L + 1)) + ((32 * e + lane) >> (L + 1));
+      const typename Tw<Op>::T w = stw[k];
+      const E other = __shfl_xor_sync(0xFFFFFFFFu, v[e], len);
+      const E x = upper ? other : v[e];
+      const E y = upper ? v[e] : other;
+      if constexpr (!INV) {
+        const E t = Tw<Op>::mul(y, w, c);
+        v[e] = upper ? sub_n<E>(x, t, N) : add_n<E>(x, t, N);
+      } else {
+        v[e] = upper ? Tw<Op>::mul(sub_n<E>(x, y, N), w, c) : add_n<E>(x, y, N);
+      }
+    }
+  }
+}
+
+template <class Op, int LOG2N, bool INV, int L>
+__device__ __forceinline__ void layers_fwd(typename Op::E (&v)[(1 << LOG2N) / 32],
+                                           const typename Tw<Op>::T* stw, int lane,
+                                           const typename Op::C& c) {
+  layer<Op, LOG2N, L, false>(v, stw, lane, c);
+  if constexpr (L > 0) layers_fwd<Op, LOG2N, INV, L - 1>(v, stw, lane, c);
+}
+
+template <class Op, int LOG2N, int L>
+__device__ __forceinline__ void layers_inv(typename Op::E (&v)[(1 << LOG2N) / 32],
+                                           const typename Tw<Op>::T* stw, int lane,
+                                           const typename Op::C& c) {
+  layer<Op, LOG2N, L, true>(v, stw, lane, c);
+  if constexpr (L + 1 < LOG2N) layers_inv<Op, LOG2N, L + 1>(v, stw, lane, c);
+}
+
+template <class Op, int LOG2N, bool INV>
+__global__ void __launch_bounds__(256) ntt_kernel(const typename Op::E* __restrict__ in,
+                                                  typename Op::E* __restrict__ out, size_t batch,
+                                                  const typename Tw<Op>::T* __restrict__ tw,
+                                                  const typename Tw<Op>::T scale,
+                                                  const typename Op::C c) {
+  using E = typename Op::E;
+  using T = typename Tw<Op>::T;
+  constexpr int n = 1 << LOG2N;
+  constexpr int EPT = n / 32;
+  __shared__ T stw[n];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) stw[i] = tw[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const size_t warp = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const size_t nwarps = (static_cast<size_t>(gridDim.x) * blockDim.x) >> 5;
+  for (size_t p = warp; p < batch; p += nwarps) {
+    const E* src = in + p * n;
+    E v[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) v[e] = src[lane + 32 * e];
+    if constexpr (!INV) {
+      layers_fwd<Op, LOG2N, INV, LOG2N - 1>(v, stw, lane, c);
+    } else {
+      layers_inv<Op, LOG2N, 0>(v, stw, lane, c);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = Tw<Op>::mul(v[e], scale, c);
+    }
+    E* dst = out + p * n;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) dst[lane + 32 * e] = v[e];
+  }
+}
+
+// ------------------------------------------------------------ phased kernel
+//
+// For n >= 64 each lane holds EPT = n/32 coefficients, so K = log2(n) - 5
+// index bits can vary inside a lane.  The transform runs in phases; phase ph
+// puts the index bits [lo, lo + K), lo = max(0, m - (ph + 1) K), inside the
+// lane (element e supplies them) and the other five bits in the lane number:
+//     i(ph, lane, e) = ((lane >> lo) << (lo + K)) | (e << lo) | (lane & (2^lo - 1)),
+// so every butterfly of the phase's layers pairs two registers of one lane.
+// Between phases the warp rewrites its coefficients through shared memory
+// (one plane of 32-bit words per word of the element; address i + 4 (i >> 5)
+// spreads a phase's accesses over the banks).  Phase 0 is i = 32 e + lane
+// (coalesced element loads), the last phase is i = EPT lane + e (each lane
+// owns EPT consecutive coefficients: vector accesses).
+
+template <int LOG2N>
+struct Phases {
+  static constexpr int m = LOG2N;
+  static constexpr int K = LOG2N - 5;
+  static constexpr int EPT = 1 << K;
+  static constexpr int count = (m + K - 1) / K;
+  __host__ __device__ static constexpr int lo(int ph) { return m - (ph + 1) * K > 0 ? m - (ph + 1) * K : 0; }
+  __host__ __device__ static constexpr int top(int ph) { return m - ph * K; }   // bits [bottom, top) butterflied in ph
+  __host__ __device__ static constexpr int bottom(int ph) { return lo(ph); }
+  __host__ __device__ static constexpr int pad(int n) { return n + (n >> 3); }
+};
+
+__device__ __forceinline__ int swz(int i) { return i + ((i >> 5) << 2); }
+
+template <int LOG2N>
+__device__ __forceinline__ int index_of(int lo, int lane, int e) {
+  constexpr int K = LOG2N - 5;
+  return ((lane >> lo) << (lo + K)) | (e << lo) | (lane & ((1 << lo) - 1));
+}
+
+template <class E>
+struct Planes;
+template <>
+struct Planes<uint32_t> {
+  static constexpr int count = 1;
+  static __device__ __forceinline__ void put(uint32_t* b, int stride, int a, uint32_t v) { b[a] = v; }
+  static __device__ __forceinline__ uint32_t get(const uint32_t* b, int stride, int a) { return b[a]; }
+};
+template <>
+struct Planes<uint64_t> {
+  static constexpr int count = 2;
+  static __device__ __forceinline__ void put(uint32_t* b, int stride, int a, uint64_t v) {
+    b[a] = static_cast<uint32_t>(v);
+    b[stride + a] = static_cast<uint32_t>(v >> 32);
+  }
+  static __device__ __forceinline__ uint64_t get(const uint32_t* b, int stride, int a) {
+    return static_cast<uint64_t>(b[a]) | (static_cast<uint64_t>(b[stride + a]) << 32);
+  }
+};
+
+// Move the lane's coefficients from phase layout `from` to layout `to`.
+template <class E, int LOG2N>
+__device__ __forceinline__ void transpose(E (&v)[1 << (LOG2N - 5)], uint32_t* buf, int lane,
+                                          int lo_from, int lo_to) {
+  constexpr int EPT = 1 << (LOG2N - 5);
+  constexpr int stride = Phases<LOG2N>::pad(1 << LOG2N);
+#pragma unroll
+  for (int e = 0; e < EPT; ++e)
+    Planes<E>::put(buf, stride, swz(index_of<LOG2N>(lo_from, lane, e)), v[e]);
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < EPT; ++e)
+    v[e] = Planes<E>::get(buf, stride, swz(index_of<LOG2N>(lo_to, lane, e)));
+  __syncwarp();
+}
+
+// All layers of bits [bottom, top) in phase layout lo; descending for the
+// forward transform, ascending for the inverse.
+template <class Op, int LOG2N, bool INV>
+__device__ __forceinline__ void phase_layers(typename Op::E (&v)[1 << (LOG2N - 5)],
+                                             const typename Tw<Op>::T* stw, int lane, int lo,
+                                             int bottom, int top, const typename Op::C& c) {
+  using E = typename Op::E;
+  constexpr int n = 1 << LOG2N;
+  constexpr int EPT = n / 32;
+  const E N = static_cast<E>(c.N);
+#pragma unroll
+  for (int step = 0; step < LOG2N; ++step) {
+    const int L = INV ? bottom + step : top - 1 - step;
+    if (L < bottom || L >= top) continue;
+    const int h = 1 << (L - lo);   // partner register distance
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      if ((e & h) == 0) {
+        const int i = index_of<LOG2N>(lo, lane, e);
+        const typename Tw<Op>::T w = stw[(n >> (L + 1)) + (i >> (L + 1))];
+        const E x = v[e], y = v[e + h];
+        if constexpr (!INV) {
+          const E t = Tw<Op>::mul(y, w, c);
+          v[e] = add_n<E>(x, t, N);
+          v[e + h] = sub_n<E>(x, t, N);
+        } else {
+          v[e] = add_n<E>(x, y, N);
+          v[e + h] = Tw<Op>::mul(sub_n<E>(x, y, N), w, c);
+        }
+      }
+    }
+  }
+}
+
+template <class Op, int LOG2N, bool INV>
+__global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* __restrict__ in,
+                                                         typename Op::E* __restrict__ out,
+                                                         size_t batch,
+                                                         const typename Tw<Op>::T* __restrict__ tw,
+                                                         const typename Tw<Op>::T scale,
+                                                         const typename Op::C c) {
+  using E = typename Op::E;
+  using T = typename Tw<Op>::T;
+  using P = Phases<LOG2N>;
+  constexpr int n = 1 << LOG2N;
+  constexpr int EPT = P::EPT;
+  constexpr int per_warp = Planes<E>::count * P::pad(n);
+  __shared__ T stw[n];
+  extern __shared__ uint32_t dyn_buf[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) stw[i] = tw[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  uint32_t* buf = dyn_buf + (threadIdx.x >> 5) * per_warp;
+  const size_t warp = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const size_t nwarps = (static_cast<size_t>(gridDim.x) * blockDim.x) >> 5;
+  constexpr int last = P::count - 1;
+  for (size_t p = warp; p < batch; p += nwarps) {
+    E v[EPT];
+    if constexpr (!INV) {
+      const E* src = in + p * n;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = src[lane + 32 * e];   // phase-0 layout
+#pragma unroll
+      for (int ph = 0; ph < P::count; ++ph) {
+        if (ph > 0) transpose<E, LOG2N>(v, buf, lane, P::lo(ph - 1), P::lo(ph));
+        phase_layers<Op, LOG2N, false>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
+      }
+      E* dst = out + p * n + lane * EPT;                          // last layout: contiguous
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) dst[e] = v[e];
+    } else {
+      const E* src = in + p * n + lane * EPT;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = src[e];
+#pragma unroll
+      for (int ph = last; ph >= 0; --ph) {
+        if (ph < last) transpose<E, LOG2N>(v, buf, lane, P::lo(ph + 1), P::lo(ph));
+        phase_layers<Op, LOG2N, true>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
+      }
+      E* dst = out + p * n;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) dst[lane + 32 * e] = Tw<Op>::mul(v[e], scale, c);
+    }
+  }
+}
+
+// ------------------------------------------------------------ host tables
+
+using u128h = unsigned __int128;
+
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t N) {
+  return static_cast<uint64_t>((static_cast<u128h>(a) * b) % N);
+}
+uint64_t powmod(uint64_t a, uint64_t e, uint64_t N) {
+  uint64_t r = 1 % N;
+  a %= N;
+  while (e) {
+    if (e & 1) r = mulmod(r, a, N);
+    a = mulmod(a, a, N);
+    e >>= 1;
+  }
+  return r;
+}
+uint32_t bitrev(uint32_t k, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; ++i) r = (r << 1) | ((k >> i) & 1u);
+  return r;
+}
+
+template <class Op, int LOG2N, bool INV>
+cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, const void* scale,
+                       const typename Op::C& c, cudaStream_t s) {
+  using T = typename Tw<Op>::T;
+  using E = typename Op::E;
+  const size_t warps_per_block = 8;
+  const size_t want = (batch + warps_per_block - 1) / warps_per_block;
+  if constexpr (LOG2N == 5) {   // one coefficient per lane: the shuffle kernel
+    const void* k = reinterpret_cast<const void*>(ntt_kernel<Op, LOG2N, INV>);
+    const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256);
+    ntt_kernel<Op, LOG2N, INV><<<static_cast<unsigned>(want < cap ? want : cap), 256, 0, s>>>(
+        static_cast<const E*>(in), static_cast<E*>(out), batch, static_cast<const T*>(tw),
+        *static_cast<const T*>(scale), c);
+  } else {
+    auto kernel = ntt_phased_kernel<Op, LOG2N, INV>;
+    const size_t smem = warps_per_block * Planes<E>::count *
+                        static_cast<size_t>(Phases<LOG2N>::pad(1 << LOG2N)) * sizeof(uint32_t);
+    static bool attr_set = false;   // opt in above 48 KB once per process
+    if (!attr_set) {
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      attr_set = true;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    const size_t cap = static_cast<size_t>(device_sm_count()) * per_sm;
+    kernel<<<static_cast<unsigned>(want < cap ? want : cap), 256, smem, s>>>(
+        static_cast<const E*>(in), static_cast<E*>(out), batch, static_cast<const T*>(tw),
+        *static_cast<const T*>(scale), c);
+  }
+  return cudaGetLastError();
+}
+
+template <class Op, bool INV>
+cudaError_t launch_ntt_n(int log2n, const void* in, void* out, size_t batch, const void* tw,
+                         const void* scale, const typename Op::C& c, cudaStream_t s) {
+  switch (log2n) {
+    case 5: return launch_ntt<Op, 5, INV>(in, out, batch, tw, scale, c, s);
+    case 6: return launch_ntt<Op, 6, INV>(in, out, batch, tw, scale, c, s);
+    case 7: return launch_ntt<Op, 7, INV>(in, out, batch, tw, scale, c, s);
+    case 8: return launch_ntt<Op, 8, INV>(in, out, batch, tw, scale, c, s);
+    case 9: return launch_ntt<Op, 9, INV>(in, out, batch, tw, scale, c, s);
+    default: return launch_ntt<Op, 10, INV>(in, out, batch, tw, scale, c, s);
+  }
+}
+
+}  // namespace
+}  // namespace montgb
+
+using namespace montgb;
+
+struct mont_ntt {
+  int variant = 0, width = 0, log2n = 0;
+  WordConst32 w32{};
+  WordConst64 w64{};
+  void* d_tables = nullptr;   // forward table, inverse table
+  size_t tw_bytes = 0;        // bytes of one table entry
+  std::vector<unsigned char> scale;  // multiplier form of n^{-1}
+};
+
+extern "C" int mont_ntt_create(mont_ntt_t* out, mont_ctx_t ctx, int log2n, const uint32_t* psi_limbs) {
+  if (!out || !ctx || !psi_limbs) return MONT_EINVAL;
+  if (log2n < 5 || log2n > 10) return MONT_EINVAL;
+  if (ctx->n_limbs > 2 || (ctx->variant != MONT_REDC && ctx->variant != MONT_PLANTARD))
+    return MONT_EINVAL;
+  const int n = 1 << log2n;
+  const uint64_t N = ctx->n_limbs == 1 ? ctx->w32.N : ctx->w64.N;
+  const uint64_t psi = ctx->n_limbs == 1 ? psi_limbs[0]
+                                         : (static_cast<uint64_t>(psi_limbs[1]) << 32) | psi_limbs[0];
+  if (psi == 0 || psi >= N) return MONT_EINVAL;
+  if (powmod(psi, static_cast<uint64_t>(n), N) != N - 1) return MONT_EINVAL;  // psi^n = -1
+  mont_ntt* p = new (std::nothrow) mont_ntt;
+  if (!p) return MONT_ENOMEM;
+  p->variant = ctx->variant;
+  p->width = ctx->width;
+  p->log2n = log2n;
+  p->w32 = ctx->w32;
+  p->w64 = ctx->w64;
+  const bool plantard = ctx->variant == MONT_PLANTARD;
+  const int w = ctx->width;
+  p->tw_bytes = (plantard ? 2 : 1) * static_cast<size_t>(w / 8);
+  // R mod N for R = 2^w (REDC) or 2^{2w} (Plantard)
+  const uint64_t r1 = static_cast<uint64_t>((u128h{1} << w) % N);  // 2^w mod N
+  const uint64_t Rmod = plantard ? mulmod(r1, r1, N) : r1;
+  const u128h ninv2 = w == 32 ? static_cast<u128h>(ctx->w32.ninv2)
+                              : (static_cast<u128h>(ctx->w64.ninv2_hi) << 64) | ctx->w64.ninv2_lo;
+  // multiplier form of a residue x: x R mod N (REDC), or (-x R mod N) N^{-1} mod R (Plantard)
+  auto form = [&](uint64_t x, unsigned char* dst) {
+    uint64_t m = mulmod(x, Rmod, N);
+    if (!plantard) {
+      if (w == 32) { const uint32_t v = static_cast<uint32_t>(m); std::memcpy(dst, &v, 4); }
+      else std::memcpy(dst, &m, 8);
+      return;
+    }
+    m = m ? N - m : 0;
+    if (w == 32) {
+      const uint64_t b = m * static_cast<uint64_t>(ninv2);   // mod 2^64
+      std::memcpy(dst, &b, 8);
+    } else {
+      const u128h b = static_cast<u128h>(m) * ninv2;         // mod 2^128
+      std::memcpy(dst, &b, 16);
+    }
+  };
+  std::vector<unsigned char> host(2 * n * p->tw_bytes);
+  const uint64_t psi_inv = powmod(psi, 2 * static_cast<uint64_t>(n) - 1, N);   // psi^{2n-1} = psi^{-1}
+  for (int k = 0; k < n; ++k) {
+    const uint64_t e = bitrev(static_cast<uint32_t>(k), log2n);
+    form(powmod(psi, e, N), &host[k * p->tw_bytes]);
+    form(powmod(psi_inv, e, N), &host[(n + k) * p->tw_bytes]);
+  }
+  p->scale.resize(p->tw_bytes);
+  // n^{-1} mod N (N odd): invert n = 2^log2n by halving 1 repeatedly
+  uint64_t ninv_n = 1;
+  for (int i = 0; i < log2n; ++i) ninv_n = (ninv_n & 1) ? static_cast<uint64_t>((static_cast<u128h>(ninv_n) + N) >> 1) : ninv_n >> 1;
+  form(ninv_n, p->scale.data());
+  cudaError_t e = cudaMalloc(&p->d_tables, host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tables, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (p->d_tables) cudaFree(p->d_tables);
+    delete p;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MONT_ENOMEM : cuda_status(e);
+  }
+  *out = p;
+  return MONT_OK;
+}
+
+extern "C" int mont_ntt_destroy(mont_ntt_t p) {
+  if (!p) return MONT_OK;
+  if (p->d_tables) cudaFree(p->d_tables);
+  delete p;
+  return MONT_OK;
+}
+
+static int ntt_run(mont_ntt_t p, const void* in, void* out, size_t batch, void* stream, bool inv) {
+  if (!p) return MONT_EINVAL;
+  if (batch == 0) return MONT_OK;
+  if (!in || !out) return MONT_EINVAL;
+  const size_t es = static_cast<size_t>(p->width / 8);
+  const size_t bytes = batch << p->log2n;
+  if (reinterpret_cast<uintptr_t>(in) % es || reinterpret_cast<uintptr_t>(out) % es) return MONT_EINVAL;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+  if (a != b && a < b + bytes * es && b < a + bytes * es) return MONT_EINVAL;
+  const char* tw = static_cast<const char*>(p->d_tables) + (inv ? (size_t{1} << p->log2n) * p->tw_bytes : 0);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  const void* sc = p->scale.data();
+  if (p->width == 32) {
+    if (p->variant == MONT_REDC)
+      e = inv ? launch_ntt_n<Redc32, true>(p->log2n, in, out, batch, tw, sc, p->w32, s)
+              : launch_ntt_n<Redc32, false>(p->log2n, in, out, batch, tw, sc, p->w32, s);
+    else
+      e = inv ? launch_ntt_n<Plantard32, true>(p->log2n, in, out, batch, tw, sc, p->w32, s)
+              : launch_ntt_n<Plantard32, false>(p->log2n, in, out, batch, tw, sc, p->w32, s);
+  } else {
+    if (p->variant == MONT_REDC)
+      e = inv ? launch_ntt_n<Redc64, true>(p->log2n, in, out, batch, tw, sc, p->w64, s)
+              : launch_ntt_n<Redc64, false>(p->log2n, in, out, batch, tw, sc, p->w64, s);
+    else
+      e = inv ? launch_ntt_n<Plantard64, true>(p->log2n, in, out, batch, tw, sc, p->w64, s)
+              : launch_ntt_n<Plantard64, false>(p->log2n, in, out, batch, tw, sc, p->w64, s);
+  }
+  return cuda_status(e);
+}
+
+extern "C" int mont_ntt_forward(mont_ntt_t p, const void* in, void* out, size_t batch, void* stream) {
+  return ntt_run(p, in, out, batch, stream, false);
+}
+
+extern "C" int mont_ntt_inverse(mont_ntt_t p, const void* in, void* out, size_t batch, void* stream) {
+  return ntt_run(p, in, out, batch, stream, true);
+}

@@ -13,10 +13,28 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
 namespace montgb {
+
+// Every variant without a prepared form (REDC, Algorithm 1: the fixed-
+// multiplier trick of Section 3.2 is Plantard's) reports kHasPre = false.
+template <class Op, class = void>
+struct HasPre { static constexpr bool value = false; };
+template <class Op>
+struct HasPre<Op, std::void_t<decltype(Op::kHasPre)>> { static constexpr bool value = Op::kHasPre; };
+
+// (a sign-extended to 64 bits) * b' mod 2^64 from 32-bit products: the low
+// word of a times b' plus the correction -b'_lo 2^32 when a < 0.
+__device__ __forceinline__ uint64_t signed_times_prepared32(int32_t a, uint64_t bp) {
+  const uint32_t ua = static_cast<uint32_t>(a);
+  const uint32_t blo = static_cast<uint32_t>(bp), bhi = static_cast<uint32_t>(bp >> 32);
+  const uint32_t lo = ua * blo;
+  const uint32_t hi = __umulhi(ua, blo) + ua * bhi - (a < 0 ? blo : 0u);
+  return (static_cast<uint64_t>(hi) << 32) | lo;
+}
 
 // ---------------------------------------------------------------------------
 // 32-bit words.  REDC and Algorithm 1 use R = 2^32; the Plantard family uses
@@ -82,6 +100,15 @@ struct Plantard32 {
     return static_cast<uint32_t>(p >> 32);
   }
   static __device__ __forceinline__ E canon(E r, const C&) { return r; }
+  // Section 3.2's fixed multiplier: b' = b N^{-1} mod 2^64, then only
+  // floor((a b' mod 2^64) / 2^32) is needed, two 32-bit products.
+  static constexpr bool kHasPre = true;
+  static __device__ __forceinline__ TT prepare(E b, const C& c) { return static_cast<uint64_t>(b) * c.ninv2; }
+  static __device__ __forceinline__ E mul_pre(E a, TT bp, const C& c) {
+    const uint32_t q = __umulhi(a, static_cast<uint32_t>(bp)) + a * static_cast<uint32_t>(bp >> 32);
+    const uint64_t p = static_cast<uint64_t>(q) * c.N + c.N;
+    return static_cast<uint32_t>(p >> 32);
+  }
 };
 
 // Algorithm 3 (SigPRedc1), R = 2^64:
@@ -102,6 +129,17 @@ struct SignedPlantard32 {
     return static_cast<int32_t>(p >> 32);
   }
   static __device__ __forceinline__ E canon(E r, const C&) { return r; }
+  static constexpr bool kHasPre = true;
+  static __device__ __forceinline__ TT prepare(E b, const C& c) {
+    return static_cast<int64_t>(static_cast<uint64_t>(static_cast<int64_t>(b)) * c.ninv2);
+  }
+  static __device__ __forceinline__ E mul_pre(E a, TT bp, const C& c) {
+    const uint64_t m = signed_times_prepared32(a, static_cast<uint64_t>(bp));
+    const int64_t q = static_cast<int64_t>(static_cast<int32_t>(m >> 32)) +
+                      static_cast<int64_t>((m >> 31) & 1u);
+    const int64_t p = q * static_cast<int64_t>(c.N) + (int64_t{1} << 31);
+    return static_cast<int32_t>(p >> 32);
+  }
 };
 
 // Algorithm 4 (SigPRedc2), R = 2^64: r = floor((floor((T Ñ^{-1} mods R)/2^32) + 2^alpha) N / 2^32).
@@ -119,6 +157,15 @@ struct SignedPlantard2_32 {
     return static_cast<int32_t>((q * static_cast<int64_t>(c.N)) >> 32);
   }
   static __device__ __forceinline__ E canon(E r, const C&) { return r; }
+  static constexpr bool kHasPre = true;
+  static __device__ __forceinline__ TT prepare(E b, const C& c) {
+    return static_cast<int64_t>(static_cast<uint64_t>(static_cast<int64_t>(b)) * c.ninv2);
+  }
+  static __device__ __forceinline__ E mul_pre(E a, TT bp, const C& c) {
+    const uint64_t m = signed_times_prepared32(a, static_cast<uint64_t>(bp));
+    const int64_t q = static_cast<int64_t>(static_cast<int32_t>(m >> 32)) + (int64_t{1} << c.alpha);
+    return static_cast<int32_t>((q * static_cast<int64_t>(c.N)) >> 32);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -183,6 +230,17 @@ struct Plantard64 {
     return static_cast<uint64_t>(p >> 64);
   }
   static __device__ __forceinline__ E canon(E r, const C&) { return r; }
+  static constexpr bool kHasPre = true;
+  static __device__ __forceinline__ TT prepare(E b, const C& c) {   // b N^{-1} mod 2^128
+    const u128 ninv = (static_cast<u128>(c.ninv2_hi) << 64) | c.ninv2_lo;
+    return static_cast<u128>(b) * ninv;
+  }
+  static __device__ __forceinline__ E mul_pre(E a, TT bp, const C& c) {
+    const uint64_t blo = static_cast<uint64_t>(bp), bhi = static_cast<uint64_t>(bp >> 64);
+    const uint64_t q = __umul64hi(a, blo) + a * bhi;
+    const u128 p = static_cast<u128>(q) * c.N + c.N;
+    return static_cast<uint64_t>(p >> 64);
+  }
 };
 
 struct SignedPlantard64 {
@@ -202,6 +260,21 @@ struct SignedPlantard64 {
     return static_cast<int64_t>(p >> 64);
   }
   static __device__ __forceinline__ E canon(E r, const C&) { return r; }
+  static constexpr bool kHasPre = true;
+  static __device__ __forceinline__ TT prepare(E b, const C& c) {
+    const u128 ninv = (static_cast<u128>(c.ninv2_hi) << 64) | c.ninv2_lo;
+    return static_cast<i128>(static_cast<u128>(static_cast<i128>(b)) * ninv);
+  }
+  static __device__ __forceinline__ E mul_pre(E a, TT bp, const C& c) {
+    const uint64_t ua = static_cast<uint64_t>(a);
+    const uint64_t blo = static_cast<uint64_t>(bp);
+    const uint64_t bhi = static_cast<uint64_t>(static_cast<u128>(bp) >> 64);
+    const uint64_t ml = ua * blo;
+    const int64_t mh = static_cast<int64_t>(__umul64hi(ua, blo) + ua * bhi - (a < 0 ? blo : 0u));
+    const i128 p = static_cast<i128>(mh) * static_cast<int64_t>(c.N) +
+                   ((ml >> 63) ? static_cast<i128>(c.N) : i128{0}) + (i128{1} << 63);
+    return static_cast<int64_t>(p >> 64);
+  }
 };
 
 struct SignedPlantard2_64 {
@@ -219,6 +292,20 @@ struct SignedPlantard2_64 {
     return static_cast<int64_t>(p >> 64);
   }
   static __device__ __forceinline__ E canon(E r, const C&) { return r; }
+  static constexpr bool kHasPre = true;
+  static __device__ __forceinline__ TT prepare(E b, const C& c) {
+    const u128 ninv = (static_cast<u128>(c.ninv2_hi) << 64) | c.ninv2_lo;
+    return static_cast<i128>(static_cast<u128>(static_cast<i128>(b)) * ninv);
+  }
+  static __device__ __forceinline__ E mul_pre(E a, TT bp, const C& c) {
+    const uint64_t ua = static_cast<uint64_t>(a);
+    const uint64_t blo = static_cast<uint64_t>(bp);
+    const uint64_t bhi = static_cast<uint64_t>(static_cast<u128>(bp) >> 64);
+    const int64_t mh = static_cast<int64_t>(__umul64hi(ua, blo) + ua * bhi - (a < 0 ? blo : 0u));
+    const i128 p = static_cast<i128>(mh) * static_cast<int64_t>(c.N) +
+                   (static_cast<i128>(c.N) << c.alpha);
+    return static_cast<int64_t>(p >> 64);
+  }
 };
 
 }  // namespace montgb

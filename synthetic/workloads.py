@@ -29,7 +29,7 @@ __all__ = [
     "rng", "uniform_residues", "centred_residues", "lift_unsigned", "is_probable_prime",
     "rns_primes", "log_uniform_lengths", "random_odd_modulus", "limbs_of",
     "int_of_limbs", "uniform_limb_residues", "bounded_limb_residues", "Job", "serving_jobs",
-    "REDC32_N", "WORD32_MODULI",
+    "REDC32_N", "WORD32_MODULI", "ntt_prime", "primitive_2n_root",
 ]
 
 # Moduli of the 32-bit workloads: Kyber's q = 3329 and Dilithium's q = 8380417.
@@ -190,6 +190,33 @@ def bounded_limb_residues(N: int, k: int, count: int, seed: int) -> np.ndarray:
         raise ValueError("N must fill its top limb")
     out[:, k - 1] = g.integers(0, top, size=count, dtype=np.uint64).astype(np.uint32)
     return out
+
+
+def ntt_prime(bits_lo: int, bits_hi: int, two_adicity: int, seed: int) -> int:
+    """A prime 2^bits_lo <= p < 2^bits_hi with p = 1 mod 2^two_adicity."""
+    g = rng(seed)
+    step = 1 << two_adicity
+    c_lo = ((1 << bits_lo) - 1) // step + 1
+    c_hi = ((1 << bits_hi) - 2) // step
+    while True:
+        c = int(g.integers(c_lo, c_hi, dtype=np.int64, endpoint=True))
+        p = c * step + 1
+        if is_probable_prime(p):
+            return p
+
+
+def primitive_2n_root(N: int, n: int, seed: int) -> int:
+    """psi with psi^n = -1 mod N (a primitive 2n-th root of unity for a power
+    of two n), found as g^((N-1)/2n) for random g; N prime, 2n | N - 1."""
+    if (N - 1) % (2 * n):
+        raise ValueError("2n must divide N - 1")
+    g = rng(seed)
+    while True:
+        x = int(g.integers(2, N - 1, dtype=np.uint64)) if N < (1 << 63) else \
+            int(g.integers(2, 1 << 62, dtype=np.int64))
+        psi = pow(x, (N - 1) // (2 * n), N)
+        if pow(psi, n, N) == N - 1:
+            return psi
 
 
 @dataclass
