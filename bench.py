@@ -356,6 +356,79 @@ def extra_sweep(mg, stream):
     return out
 
 
+# 32-bit integer operations per butterfly: the twiddle product plus a modular
+# add and a modular subtract.  32-bit words: REDC 14 (product, m, high product
+# with N, carry add, conditional subtraction, 3 + 3), Plantard with a prepared
+# twiddle 10 (two products, one add, one product with N, 3 + 3).  64-bit words,
+# counting every 64-bit product in 32-bit multiply-adds (4 for a full or high
+# product, 3 for a low one) and 64-bit adds as 2: REDC 37, Plantard 34; see
+# the design doc
+NTT_BUTTERFLY_OPS = {(0, 32): 14, (2, 32): 10, (0, 64): 37, (2, 64): 34}
+
+
+def extra_ntt(mg, stream, peak):
+    """Batched negacyclic NTTs: 2^18 polynomials of length 256 mod 8380417
+    (32-bit words) and 2^15 of length 1024 mod a 62-bit RNS prime (64-bit
+    words), with REDC (Montgomery-form twiddles) and Plantard (prepared
+    twiddles) butterflies; plus mont_mul_pre against mont_mul."""
+    import torch
+    out = {}
+    L = mg.lib()
+    sp = stream.cuda_stream
+    rns = sy.rns_primes(1, seed=3)[0]
+    for N, w, log2n, batch in ((8380417, 32, 8, 1 << 18), (rns, 64, 10, 1 << 15)):
+        n = 1 << log2n
+        psi = sy.primitive_2n_root(N, n, seed=1)
+        dt = torch.uint32 if w == 32 else torch.uint64
+        x = torch.from_numpy(sy.uniform_residues(N, batch * n, seed=7,
+                                                 dtype=np.uint32 if w == 32 else np.uint64)).cuda()
+        y = torch.empty_like(x)
+        for v in (0, 2):
+            ctx = mg.mont_ctx_create(N, w if v == 0 else 2 * w, v)
+            plan = mg.Ntt(ctx, log2n, psi)
+            f = lambda: L.mont_ntt_forward(plan.handle, x.data_ptr(), y.data_ptr(), batch, sp)
+            g = lambda: L.mont_ntt_inverse(plan.handle, y.data_ptr(), y.data_ptr(), batch, sp)
+            for _ in range(3):
+                f()
+            ms_f = _events_ms(f, 20, stream)
+            ms_i = _events_ms(g, 20, stream)
+            bfly = batch * (n // 2) * log2n
+            ops = bfly * NTT_BUTTERFLY_OPS[(v, w)] / (ms_f * 1e-3)
+            gb = 2 * batch * n * (w // 8) / (ms_f * 1e-3) / 1e9
+            out[f"n{n}_w{w}_{'redc' if v == 0 else 'plantard'}"] = {
+                "polys": batch, "forward_us": round(ms_f * 1e3, 1), "inverse_us": round(ms_i * 1e3, 1),
+                "gcoeff_s": round(batch * n / (ms_f * 1e-3) / 1e9, 1),
+                "roofline": {"bound": "alu", "achieved": round(ops / 1e12, 2),
+                             "peak": round(ISSUE_PEAK / 1e12, 2), "unit": "T int-ops/s",
+                             "frac": round(ops / ISSUE_PEAK, 3), "hbm_frac": round(gb / peak, 3)}}
+            plan.close()
+    for tag in ("n256_w32", "n1024_w64"):
+        out[f"{tag}_plantard_speedup_over_redc"] = round(
+            out[f"{tag}_redc"]["forward_us"] / out[f"{tag}_plantard"]["forward_us"], 2)
+    # prepared multipliers on the 32-bit workload size
+    N, n = 8380417, 1 << 26
+    ctx = mg.mont_ctx_create(N, 64, 2)
+    a = torch.from_numpy(sy.uniform_residues(N, n, seed=8)).cuda()
+    b = torch.from_numpy(sy.uniform_residues(N, n, seed=9)).cuda()
+    bp = torch.empty(n, dtype=torch.uint64, device="cuda")
+    o = torch.empty_like(a)
+    mg.mont_const_prepare(ctx, b, bp)
+    fp = lambda: L.mont_mul_pre(ctx.handle, a.data_ptr(), bp.data_ptr(), o.data_ptr(), n, sp)
+    fm = lambda: L.mont_mul(ctx.handle, a.data_ptr(), b.data_ptr(), o.data_ptr(), n, sp)
+    for _ in range(3):
+        fp()
+        fm()
+    ms_p = _events_ms(fp, 50, stream)
+    ms_m = _events_ms(fm, 50, stream)
+    out["mul_pre_2p26"] = {"us": round(ms_p * 1e3, 1), "gmodmul_s": round(n / (ms_p * 1e-3) / 1e9, 1),
+                           "mont_mul_us": round(ms_m * 1e3, 1),
+                           "roofline": {"bound": "hbm", "achieved": round(16 * n / (ms_p * 1e-3) / 1e9, 1),
+                                        "peak": peak, "unit": "GB/s",
+                                        "frac": round(16 * n / (ms_p * 1e-3) / 1e9 / peak, 3),
+                                        "note": "16 B per product: a (4), b' (8), out (4)"}}
+    return out
+
+
 def extra_serving(mg, jobs_count):
     """Poisson stream of mixed jobs through the serving loop at 0.5x and 0.8x
     of the measured capacity."""
@@ -547,6 +620,7 @@ def run_ours(args):
             "rns64_batched": extra_rns64(mg, stream, peak),
             "cios": extra_cios(mg, stream, peak),
             "sweep_r16": extra_sweep(mg, stream),
+            "ntt": extra_ntt(mg, stream, peak),
             "serving": extra_serving(mg, args.serving_jobs),
         }
 

@@ -107,9 +107,11 @@ __device__ __forceinline__ bool fast_good(int32_t r, uint32_t c, const SweepN& e
 
 // The exact test: counterexample unless r = c (mod N) and r in range.
 __device__ __forceinline__ bool exact_bad(int32_t r, uint32_t c, const SweepN& e) {
+  if (r < e.r_lo || r > e.r_hi) return true;   // out of range: no congruence needed
   const int64_t d = static_cast<int64_t>(r) - static_cast<int64_t>(static_cast<int32_t>(c));
-  const bool cong = (d % static_cast<int64_t>(e.N)) == 0;
-  return !cong || r < e.r_lo || r > e.r_hi;
+  const int64_t N = e.N;
+  if (d == 0 || d == N || d == -N) return false;
+  return (d % N) != 0;
 }
 
 __device__ __forceinline__ uint32_t add_mod(uint32_t c, uint32_t s, uint32_t N) {

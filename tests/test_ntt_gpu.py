@@ -118,3 +118,27 @@ def test_ntt_rejects_bad_parameters():
     s1 = mg.mont_ctx_create(8380417, 32, 1)
     with pytest.raises(mg.MontError):
         mg.Ntt(s1, 8, sy.primitive_2n_root(8380417, 256, 1))
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_ntt_full_size_2p18_polynomials(variant):
+    """The benchmark's transform: 2^18 polynomials of length 256 mod 8380417;
+    round trip of every coefficient, sampled polynomials against the oracle."""
+    N, log2n, batch = 8380417, 8, 1 << 18
+    n = 1 << log2n
+    psi = sy.primitive_2n_root(N, n, seed=1)
+    ctx = mg.mont_ctx_create(N, 32 if variant == 0 else 64, variant)
+    plan = mg.Ntt(ctx, log2n, psi)
+    x = torch.from_numpy(sy.uniform_residues(N, batch * n, seed=7)).cuda()
+    y = torch.empty_like(x)
+    plan.forward(x, y)
+    z = torch.empty_like(x)
+    plan.inverse(y, z)
+    sync()
+    assert torch.equal(z, x)
+    xs = x.view(torch.int32).cpu().numpy()
+    ys = y.view(torch.int32).cpu().numpy()
+    rnd = random.Random(variant)
+    for p in [0, batch - 1] + [rnd.randrange(batch) for _ in range(3)]:
+        poly = [int(v) for v in xs[p * n:(p + 1) * n]]
+        assert [int(v) for v in ys[p * n:(p + 1) * n]] == on.ntt_forward(poly, N, psi), p
