@@ -190,6 +190,22 @@ int mont_const_prepare(mont_ctx_t ctx, const void* b, void* b_pre, size_t n, voi
 int mont_mul_pre(mont_ctx_t ctx, const void* a, const void* b_pre, void* out, size_t n,
                  void* stream);
 
+/* ------------------------------------------------------- lazy reduction */
+/*
+ * mont_dot_lazy -- out[j] = SigPRedc2(sum_{i<k} a[j k + i] b[j k + i]): row dot
+ * products reduced once each with Algorithm 4, which Section 3.3 proves
+ * correct for |T| <= 2^{2 alpha} N^2 (alpha >= 1).  With inputs in the mods-N
+ * range each product has |a b| <= N^2/4, so any k <= 4^{alpha+1} keeps the
+ * sum within that bound; the result is -(sum a b) R^{-1} mods N.
+ *
+ *   ctx   MONT_SIGNED_PLANTARD2 at 32- or 64-bit words (its alpha sets the
+ *         largest k); MONT_EINVAL otherwise or when k = 0 or k > 4^{alpha+1}.
+ *   a, b  device arrays of rows * k elements, row-major; out: device array of
+ *         `rows` elements, not overlapping a or b.  Asynchronous.
+ */
+int mont_dot_lazy(mont_ctx_t ctx, const void* a, const void* b, void* out, size_t rows,
+                  uint32_t k, void* stream);
+
 /* ------------------------------------------------------------------ NTT */
 /*
  * Batched negacyclic number-theoretic transform over Z_N, the application the

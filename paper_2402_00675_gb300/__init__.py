@@ -180,6 +180,7 @@ def _declare(L):
         "mont_ntt_forward": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_ntt_inverse": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_ntt_destroy": (_int, [_vp]),
+        "mont_dot_lazy": (_int, [_vp, _vp, _vp, _vp, _sz, _c.c_uint32, _vp]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -644,6 +645,14 @@ class Ntt:
 
 def mont_ntt_create(ctx: Ctx, log2n: int, psi: int) -> Ntt:
     return Ntt(ctx, log2n, psi)
+
+
+def mont_dot_lazy(ctx: Ctx, a, b, out, k: int, rows: int | None = None, stream=None) -> None:
+    """out[j] = Algorithm 4 applied once to a row dot product (see montgb.h)."""
+    if rows is None:
+        rows = _count(ctx, out, None)
+    _check(lib().mont_dot_lazy(ctx, _ptr(a), _ptr(b), _ptr(out), rows, k, _stream(stream)),
+           "mont_dot_lazy")
 
 
 def mont_sync(stream=None) -> None:
