@@ -22,12 +22,14 @@ montgomery : definitions, constants, REDC and Algorithms 1-4, domain maps.
 exhaustive : exhaustive counterexample search of Section 3 (Example 3.1).
 ntt        : Plantard's fixed-multiplier form (Section 3.2) and the negacyclic
              number-theoretic transform it serves (definitions, O(n^2)).
+rns        : residue-number-system conversions by the CRT formula (Section 2).
 
 Parity status: every public function is pinned by ``tests/test_oracle_pins.py``
 (Qin's identity, Example 3.1, brute force over tiny moduli, the range theorems
 and the inequality criterion of Section 3.3) and ``tests/test_oracle_ntt_pins.py``
 (exhaustive prepared-multiplier products, a hand-derived transform, the
-negacyclic convolution theorem).  No function is parity-unpinned.
+negacyclic convolution theorem) and ``tests/test_oracle_rns_pins.py`` (search on
+tiny moduli, the two-modulus formula of Eq. (2)).  No function is parity-unpinned.
 """
 
 from .montgomery import (  # noqa: F401
@@ -39,4 +41,4 @@ from .montgomery import (  # noqa: F401
     from_limbs, to_limbs,
 )
 from .exhaustive import sweep, SweepResult, count_candidate_failures_np  # noqa: F401
-from . import ntt  # noqa: F401
+from . import ntt, rns  # noqa: F401

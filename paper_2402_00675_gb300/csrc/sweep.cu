@@ -132,15 +132,17 @@ __device__ __forceinline__ uint32_t step_ref(uint32_t c, uint32_t s, uint32_t N)
   else return add_mod(c, s, N);
 }
 
+// Append one counterexample; returns true once the buffer is seen full, after
+// which the caller stops calling (so a sweep with many failures pays only for
+// counting them).
 template <bool kUnsignedTarget>
-__device__ __noinline__ void record(int32_t T, int32_t r, uint32_t c, uint32_t N,
+__device__ __noinline__ bool record(int32_t T, int32_t r, uint32_t c, uint32_t N,
                                     mont_cex* __restrict__ cex,
                                     unsigned long long* __restrict__ cex_n,
-                                    unsigned long long cap, bool* full) {
-  if (!*full && *reinterpret_cast<volatile unsigned long long*>(cex_n) >= cap) *full = true;
-  if (*full) return;
+                                    unsigned long long cap) {
+  if (*reinterpret_cast<volatile unsigned long long*>(cex_n) >= cap) return true;
   const unsigned long long slot = atomicAdd(cex_n, 1ull);
-  if (slot >= cap) return;
+  if (slot >= cap) return true;
   // c is in [0, N) or, for a centred chain, already in [-(N-1)/2, (N-1)/2]
   int64_t expect = static_cast<int32_t>(c);
   if (expect < 0) expect += N;
@@ -152,6 +154,7 @@ __device__ __noinline__ void record(int32_t T, int32_t r, uint32_t c, uint32_t N
   rec.r = r;
   rec.expected = expect;
   cex[slot] = rec;
+  return false;
 }
 
 template <int V, int RK>
@@ -201,10 +204,16 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
       const bool ga = fast_good<RK>(ra, c0, e), gb = fast_good<RK>(rb, c1, e);
       const bool gc = fast_good<RK>(rc, c2, e), gd = fast_good<RK>(rd, c3, e);
       if (!(ga && gb && gc && gd)) {
-        if (!ga && exact_bad(ra, c0, e)) { ++local; record<kUnsignedTarget>(Ta, ra, c0, N, cex, cex_n, cap, &full); }
-        if (!gb && exact_bad(rb, c1, e)) { ++local; record<kUnsignedTarget>(Tb, rb, c1, N, cex, cex_n, cap, &full); }
-        if (!gc && exact_bad(rc, c2, e)) { ++local; record<kUnsignedTarget>(Tc, rc, c2, N, cex, cex_n, cap, &full); }
-        if (!gd && exact_bad(rd, c3, e)) { ++local; record<kUnsignedTarget>(Td, rd, c3, N, cex, cex_n, cap, &full); }
+        const bool ba = !ga && exact_bad(ra, c0, e), bb = !gb && exact_bad(rb, c1, e);
+        const bool bc = !gc && exact_bad(rc, c2, e), bd = !gd && exact_bad(rd, c3, e);
+        local += static_cast<uint32_t>(ba) + static_cast<uint32_t>(bb) + static_cast<uint32_t>(bc) +
+                 static_cast<uint32_t>(bd);
+        if (!full && (ba || bb || bc || bd)) {
+          if (ba && !full) full = record<kUnsignedTarget>(Ta, ra, c0, N, cex, cex_n, cap);
+          if (bb && !full) full = record<kUnsignedTarget>(Tb, rb, c1, N, cex, cex_n, cap);
+          if (bc && !full) full = record<kUnsignedTarget>(Tc, rc, c2, N, cex, cex_n, cap);
+          if (bd && !full) full = record<kUnsignedTarget>(Td, rd, c3, N, cex, cex_n, cap);
+        }
       }
       c0 = step_ref<RK>(c0, s4, N);
       c1 = step_ref<RK>(c1, s4, N);
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
       const int32_t r = candidate<V>(T, e, p);
       if (!fast_good<RK>(r, c0, e) && exact_bad(r, c0, e)) {
         ++local;
-        record<kUnsignedTarget>(T, r, c0, N, cex, cex_n, cap, &full);
+        if (!full) full = record<kUnsignedTarget>(T, r, c0, N, cex, cex_n, cap);
       }
       c0 = step_ref<RK>(c0, s1, N);
     }
