@@ -239,6 +239,36 @@ int mont_ntt_forward(mont_ntt_t plan, const void* in, void* out, size_t batch, v
 int mont_ntt_inverse(mont_ntt_t plan, const void* in, void* out, size_t batch, void* stream);
 int mont_ntt_destroy(mont_ntt_t plan);
 
+/* ------------------------------------------------ RNS <-> big integers */
+/*
+ * Conversions between big integers and their residues modulo pairwise coprime
+ * odd moduli p_0 .. p_{count-1} (the multi-modulus CRT, which Section 2
+ * derives for two moduli from Qin's identity, Eq. (2), and states extends).
+ *
+ * mont_rns_create -- host array of `count` (1..64) odd, pairwise coprime
+ *   moduli, 3 <= p < 2^63, with product P < 2^2048.  Precomputes the Montgomery
+ *   constants (R = 2^64) and the partial products p_0 .. p_{i-1}, copied to a
+ *   device allocation owned by the object (synchronous).  MONT_EINVAL otherwise.
+ * mont_rns_query -- number of moduli, and `limbs`: the 32-bit limbs of every
+ *   big integer these calls read or write (8, 16, 32 or 64; at least P's).
+ * mont_rns_to_residues -- residues[i n + e] = X_e mod p_i for n big integers X
+ *   (element e at X[e limbs .. (e+1) limbs), little-endian, any value below
+ *   2^(32 limbs)).  X 16-byte aligned, residues 8-byte aligned, not
+ *   overlapping; device pointers; asynchronous.
+ * mont_rns_from_residues -- X_e = the unique integer in [0, P) with
+ *   X_e = residues[i n + e] (mod p_i) for all i; residues must lie in [0, p_i).
+ *   Same layout rules; asynchronous.
+ * mont_rns_destroy -- free the object (NULL accepted).
+ */
+typedef struct mont_rns* mont_rns_t;
+int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int count);
+int mont_rns_query(mont_rns_t rns, int* count, int* limbs);
+int mont_rns_to_residues(mont_rns_t rns, const uint32_t* X, uint64_t* residues, size_t n,
+                         void* stream);
+int mont_rns_from_residues(mont_rns_t rns, const uint64_t* residues, uint32_t* X, size_t n,
+                           void* stream);
+int mont_rns_destroy(mont_rns_t rns);
+
 /* ---------------------------------------------------------- batched RNS */
 /*
  * mont_mul_batched -- many independent mont_mul problems in one persistent

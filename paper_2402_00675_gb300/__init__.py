@@ -181,6 +181,11 @@ def _declare(L):
         "mont_ntt_inverse": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_ntt_destroy": (_int, [_vp]),
         "mont_dot_lazy": (_int, [_vp, _vp, _vp, _vp, _sz, _c.c_uint32, _vp]),
+        "mont_rns_create": (_int, [_c.POINTER(_vp), _c.POINTER(_c.c_uint64), _int]),
+        "mont_rns_query": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int)]),
+        "mont_rns_to_residues": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_rns_from_residues": (_int, [_vp, _vp, _vp, _sz, _vp]),
+        "mont_rns_destroy": (_int, [_vp]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -653,6 +658,42 @@ def mont_dot_lazy(ctx: Ctx, a, b, out, k: int, rows: int | None = None, stream=N
         rows = _count(ctx, out, None)
     _check(lib().mont_dot_lazy(ctx, _ptr(a), _ptr(b), _ptr(out), rows, k, _stream(stream)),
            "mont_dot_lazy")
+
+
+class Rns:
+    """A mont_rns_t: conversions between big integers and residues."""
+
+    def __init__(self, moduli):
+        arr = (ctypes.c_uint64 * len(moduli))(*[int(p) for p in moduli])
+        h = ctypes.c_void_p()
+        _check(lib().mont_rns_create(ctypes.byref(h), arr, len(moduli)), "mont_rns_create")
+        self.handle = h.value
+        c, k = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mont_rns_query(self.handle, ctypes.byref(c), ctypes.byref(k)), "mont_rns_query")
+        self.count, self.limbs = c.value, k.value
+
+    def to_residues(self, X, residues, n: int, stream=None) -> None:
+        _check(lib().mont_rns_to_residues(self.handle, _ptr(X), _ptr(residues), n, _stream(stream)),
+               "mont_rns_to_residues")
+
+    def from_residues(self, residues, X, n: int, stream=None) -> None:
+        _check(lib().mont_rns_from_residues(self.handle, _ptr(residues), _ptr(X), n,
+                                            _stream(stream)), "mont_rns_from_residues")
+
+    def close(self):
+        if self.handle:
+            lib().mont_rns_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mont_rns_create(moduli) -> Rns:
+    return Rns(moduli)
 
 
 def mont_sync(stream=None) -> None:

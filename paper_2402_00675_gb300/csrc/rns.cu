@@ -1,0 +1,310 @@
+// Residue-number-system conversions (mont_rns_*): the multi-modulus CRT that
+// Section 2 derives in the two-modulus case from Qin's identity.
+//
+// Big integer -> residues.  X mod p = sum_j X_j 2^{32 j} mod p over the 32-bit
+// limbs X_j.  With c_j = 2^{32 j} R mod p (R = 2^64), REDC(sum_j X_j c_j) =
+// X mod p: the sum of k products of a limb and a word stays below k 2^32 p <
+// p R, so it is accumulated exactly in 128 bits and reduced once.  One thread
+// per (element, modulus); consecutive threads take consecutive elements of one
+// modulus, so residue stores are coalesced, and a tile of 256 elements is
+// converted for every modulus before the next tile, so its limbs stay in L2.
+//
+// Residues -> big integer.  Mixed radix (Garner): X = sum_i v_i Pi_i with
+// Pi_i = p_0 ... p_{i-1} and v_i = (x_i - X_{<i}) Pi_i^{-1} mod p_i, where
+// X_{<i} = sum_{j<i} v_j Pi_j is the partial value already built.  One thread
+// per element keeps X in registers as 32-bit limbs; each step reduces X_{<i}
+// modulo p_i with the lazy accumulation above, forms v_i with one REDC
+// (Pi_i^{-1} kept in Montgomery form), and adds v_i Pi_i limb by limb.  The
+// result is the unique X in [0, P), P = prod p_i, with no quotient estimate
+// and no correction step.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "word_kernel.cuh"
+
+namespace montgb {
+namespace {
+
+constexpr int kRnsMaxModuli = 64;
+
+template <int K>
+__global__ void __launch_bounds__(256) rns_to_kernel(const uint32_t* __restrict__ X,
+                                                     uint64_t* __restrict__ res, size_t n,
+                                                     int count,
+                                                     const WordConst64* __restrict__ mods,
+                                                     const uint64_t* __restrict__ c) {
+  const size_t tiles = (n + 255) / 256;
+  const size_t total = tiles * static_cast<size_t>(count) * 256;
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+       q += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t t = q % 256;
+    const size_t rest = q / 256;
+    const int i = static_cast<int>(rest % count);
+    const size_t e = (rest / count) * 256 + t;
+    if (e >= n) continue;
+    const uint4* x = reinterpret_cast<const uint4*>(X + e * K);
+    const uint64_t* ci = c + static_cast<size_t>(i) * K;
+    u128 acc = 0;
+#pragma unroll
+    for (int j = 0; j < K / 4; ++j) {
+      const uint4 v = x[j];
+      acc += static_cast<u128>(v.x) * __ldg(ci + 4 * j);
+      acc += static_cast<u128>(v.y) * __ldg(ci + 4 * j + 1);
+      acc += static_cast<u128>(v.z) * __ldg(ci + 4 * j + 2);
+      acc += static_cast<u128>(v.w) * __ldg(ci + 4 * j + 3);
+    }
+    res[static_cast<size_t>(i) * n + e] = Redc64::reduce(acc, mods[i]);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) rns_from_kernel(const uint64_t* __restrict__ res,
+                                                       uint32_t* __restrict__ X, size_t n,
+                                                       int count,
+                                                       const WordConst64* __restrict__ mods,
+                                                       const uint64_t* __restrict__ c,
+                                                       const uint32_t* __restrict__ pi,
+                                                       const uint64_t* __restrict__ inv) {
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t x[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) x[j] = 0;
+    for (int i = 0; i < count; ++i) {
+      const WordConst64 m = mods[i];
+      const uint64_t* ci = c + static_cast<size_t>(i) * K;
+      const uint32_t* pii = pi + static_cast<size_t>(i) * K;
+      // r = X_{<i} mod p_i
+      u128 acc = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc += static_cast<u128>(x[j]) * __ldg(ci + j);
+      const uint64_t r = Redc64::reduce(acc, m);
+      const uint64_t xi = res[static_cast<size_t>(i) * n + e];
+      const uint64_t d = xi >= r ? xi - r : xi + (m.N - r);
+      // v_i = (x_i - r) Pi_i^{-1} mod p_i   (inv holds Pi_i^{-1} R mod p_i)
+      const uint64_t v = Redc64::reduce(static_cast<u128>(d) * __ldg(inv + i), m);
+      // X += v_i Pi_i; v Pi_j + x_j + carry < 2^95 + 2^64, so the carry fits a word
+      uint64_t carry = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const u128 t = static_cast<u128>(v) * __ldg(pii + j) + x[j] + carry;
+        x[j] = static_cast<uint32_t>(t);
+        carry = static_cast<uint64_t>(t >> 32);
+      }
+    }
+    uint4* out = reinterpret_cast<uint4*>(X + e * K);
+#pragma unroll
+    for (int j = 0; j < K / 4; ++j) out[j] = make_uint4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+  }
+}
+
+// ------------------------------------------------------------- host helpers
+
+using u128h = unsigned __int128;
+
+uint64_t gcd64(uint64_t a, uint64_t b) {
+  while (b) {
+    const uint64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t p) {
+  return static_cast<uint64_t>(static_cast<u128h>(a) * b % p);
+}
+uint64_t invmod64(uint64_t a, uint64_t p) {   // a^{-1} mod p, gcd(a, p) = 1
+  __int128 r0 = p, r1 = a % p, s0 = 0, s1 = 1;
+  while (r1 != 0) {
+    const __int128 q = r0 / r1;
+    __int128 t = r0 - q * r1; r0 = r1; r1 = t;
+    t = s0 - q * s1; s0 = s1; s1 = t;
+  }
+  __int128 s = s0 % static_cast<__int128>(p);
+  if (s < 0) s += p;
+  return static_cast<uint64_t>(s);
+}
+
+template <int K>
+cudaError_t launch_to(const uint32_t* X, uint64_t* res, size_t n, int count, const WordConst64* mods,
+                      const uint64_t* c, cudaStream_t s) {
+  const void* k = reinterpret_cast<const void*>(rns_to_kernel<K>);
+  const size_t total = (n + 255) / 256 * static_cast<size_t>(count) * 256;
+  const size_t want = (total + 255) / 256;
+  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256);
+  rns_to_kernel<K><<<static_cast<unsigned>(std::min(want, cap)), 256, 0, s>>>(X, res, n, count, mods, c);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_from(const uint64_t* res, uint32_t* X, size_t n, int count,
+                        const WordConst64* mods, const uint64_t* c, const uint32_t* pi,
+                        const uint64_t* inv, cudaStream_t s) {
+  const void* k = reinterpret_cast<const void*>(rns_from_kernel<K>);
+  const size_t want = (n + 255) / 256;
+  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256);
+  rns_from_kernel<K><<<static_cast<unsigned>(std::min(want, cap)), 256, 0, s>>>(
+      res, X, n, count, mods, c, pi, inv);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace montgb
+
+using namespace montgb;
+
+struct mont_rns {
+  int count = 0;
+  int limbs = 0;                 // K: limbs of every big integer (>= those of P)
+  void* dev = nullptr;           // one allocation: mods, c, pi, inv
+  WordConst64* d_mods = nullptr;
+  uint64_t* d_c = nullptr;
+  uint32_t* d_pi = nullptr;
+  uint64_t* d_inv = nullptr;
+};
+
+extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int count) {
+  if (!out || !moduli || count < 1 || count > kRnsMaxModuli) return MONT_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    const uint64_t p = moduli[i];
+    if (p < 3 || !(p & 1) || (p >> 63)) return MONT_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (gcd64(p, moduli[j]) != 1) return MONT_EINVAL;
+  }
+  // Pi_i = p_0 ... p_{i-1} as 32-bit limbs, and P = Pi_count
+  std::vector<std::vector<uint32_t>> Pi(count + 1);
+  Pi[0] = {1u};
+  for (int i = 0; i < count; ++i) {
+    const std::vector<uint32_t>& a = Pi[i];
+    std::vector<uint32_t> r(a.size() + 2, 0u);
+    const uint64_t p = moduli[i];
+    u128h carry = 0;
+    for (size_t j = 0; j < r.size(); ++j) {
+      const u128h t = (j < a.size() ? static_cast<u128h>(a[j]) * p : 0) + carry;
+      r[j] = static_cast<uint32_t>(t);
+      carry = t >> 32;
+    }
+    while (r.size() > 1 && r.back() == 0) r.pop_back();
+    Pi[i + 1] = r;
+  }
+  const int needed = static_cast<int>(Pi[count].size());
+  int K = 8;
+  while (K < needed) K *= 2;
+  if (K > 64) return MONT_EINVAL;   // P above 2^2048
+
+  std::vector<WordConst64> mods(count);
+  std::vector<uint64_t> c(static_cast<size_t>(count) * K);
+  std::vector<uint32_t> pi(static_cast<size_t>(count) * K, 0u);
+  std::vector<uint64_t> inv(count);
+  for (int i = 0; i < count; ++i) {
+    const uint64_t p = moduli[i];
+    WordConst64 m{};
+    m.N = p;
+    uint64_t x = p;   // N^{-1} mod 2^64 by Newton-Hensel
+    for (int it = 0; it < 6; ++it) x *= 2 - p * x;
+    m.ninv = x;
+    m.nprime = 0 - x;
+    m.half = (p - 1) / 2;
+    mods[i] = m;
+    const uint64_t r64 = static_cast<uint64_t>((static_cast<u128h>(1) << 64) % p);   // R mod p
+    const uint64_t two32 = static_cast<uint64_t>((static_cast<u128h>(1) << 32) % p);
+    uint64_t cj = r64;   // 2^{32 j} R mod p
+    for (int j = 0; j < K; ++j) {
+      c[static_cast<size_t>(i) * K + j] = cj;
+      cj = mulmod64(cj, two32, p);
+    }
+    for (size_t j = 0; j < Pi[i].size(); ++j) pi[static_cast<size_t>(i) * K + j] = Pi[i][j];
+    uint64_t pim = 1 % p;   // Pi_i mod p
+    for (int j = 0; j < i; ++j) pim = mulmod64(pim, moduli[j] % p, p);
+    inv[i] = mulmod64(invmod64(pim, p), r64, p);   // Montgomery form of Pi_i^{-1}
+  }
+  mont_rns* r = new (std::nothrow) mont_rns;
+  if (!r) return MONT_ENOMEM;
+  r->count = count;
+  r->limbs = K;
+  const size_t b_mods = count * sizeof(WordConst64);
+  const size_t b_c = c.size() * sizeof(uint64_t);
+  const size_t b_pi = pi.size() * sizeof(uint32_t);
+  const size_t b_inv = inv.size() * sizeof(uint64_t);
+  const size_t off_c = (b_mods + 255) / 256 * 256;
+  const size_t off_pi = off_c + (b_c + 255) / 256 * 256;
+  const size_t off_inv = off_pi + (b_pi + 255) / 256 * 256;
+  cudaError_t e = cudaMalloc(&r->dev, off_inv + b_inv);
+  if (e == cudaSuccess) {
+    char* base = static_cast<char*>(r->dev);
+    r->d_mods = reinterpret_cast<WordConst64*>(base);
+    r->d_c = reinterpret_cast<uint64_t*>(base + off_c);
+    r->d_pi = reinterpret_cast<uint32_t*>(base + off_pi);
+    r->d_inv = reinterpret_cast<uint64_t*>(base + off_inv);
+    e = cudaMemcpy(r->d_mods, mods.data(), b_mods, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_c, c.data(), b_c, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_pi, pi.data(), b_pi, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_inv, inv.data(), b_inv, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    if (r->dev) cudaFree(r->dev);
+    delete r;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MONT_ENOMEM : cuda_status(e);
+  }
+  *out = r;
+  return MONT_OK;
+}
+
+extern "C" int mont_rns_query(mont_rns_t r, int* count, int* limbs) {
+  if (!r) return MONT_EINVAL;
+  if (count) *count = r->count;
+  if (limbs) *limbs = r->limbs;
+  return MONT_OK;
+}
+
+extern "C" int mont_rns_destroy(mont_rns_t r) {
+  if (!r) return MONT_OK;
+  if (r->dev) cudaFree(r->dev);
+  delete r;
+  return MONT_OK;
+}
+
+static int rns_check(mont_rns_t r, const void* big, const void* res, size_t n) {
+  if (!r) return MONT_EINVAL;
+  if (n == 0) return 1;
+  if (!big || !res) return MONT_EINVAL;
+  if (reinterpret_cast<uintptr_t>(big) % 16 || reinterpret_cast<uintptr_t>(res) % 8) return MONT_EINVAL;
+  const size_t bb = n * 4u * static_cast<size_t>(r->limbs);
+  const size_t rb = n * 8u * static_cast<size_t>(r->count);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(big), b = reinterpret_cast<uintptr_t>(res);
+  if (a < b + rb && b < a + bb) return MONT_EINVAL;
+  return 0;
+}
+
+extern "C" int mont_rns_to_residues(mont_rns_t r, const uint32_t* X, uint64_t* residues, size_t n,
+                                    void* stream) {
+  const int chk = rns_check(r, X, residues, n);
+  if (chk) return chk == 1 ? MONT_OK : chk;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (r->limbs) {
+    case 8: e = launch_to<8>(X, residues, n, r->count, r->d_mods, r->d_c, s); break;
+    case 16: e = launch_to<16>(X, residues, n, r->count, r->d_mods, r->d_c, s); break;
+    case 32: e = launch_to<32>(X, residues, n, r->count, r->d_mods, r->d_c, s); break;
+    default: e = launch_to<64>(X, residues, n, r->count, r->d_mods, r->d_c, s); break;
+  }
+  return cuda_status(e);
+}
+
+extern "C" int mont_rns_from_residues(mont_rns_t r, const uint64_t* residues, uint32_t* X, size_t n,
+                                      void* stream) {
+  const int chk = rns_check(r, X, residues, n);
+  if (chk) return chk == 1 ? MONT_OK : chk;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (r->limbs) {
+    case 8: e = launch_from<8>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
+    case 16: e = launch_from<16>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
+    case 32: e = launch_from<32>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
+    default: e = launch_from<64>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
+  }
+  return cuda_status(e);
+}
