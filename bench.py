@@ -457,6 +457,48 @@ def extra_dot(mg, stream, peak):
                          "frac": round(gb / peak, 3)}}
 
 
+def extra_rns(mg, stream):
+    """Conversions between 2^17 big integers and their residues modulo the 32
+    RNS primes (product of 1950 bits, 64 limbs)."""
+    import torch
+    ps = sy.rns_primes(32, seed=3)
+    r = mg.Rns(ps)
+    n, k = 1 << 17, r.limbs
+    X = torch.from_numpy(sy.uniform_limb_residues(_product(ps), k, n, seed=13).reshape(-1)).cuda()
+    res = torch.empty(32 * n, dtype=torch.uint64, device="cuda")
+    Y = torch.empty_like(X)
+    f = lambda: r.to_residues(X, res, n, stream)
+    g = lambda: r.from_residues(res, Y, n, stream)
+    for _ in range(3):
+        f()
+        g()
+    ms_to = _events_ms(f, 20, stream)
+    ms_from = _events_ms(g, 20, stream)
+    assert torch.equal(X, Y)
+    # 32-bit integer operations per element: to_residues 32 moduli x 64 limbs x
+    # (2 multiply-adds for a 32x64-bit product + 4 adds into the 128-bit sum) +
+    # 32 REDC (~30); from_residues twice that plus 32 x 64 limb updates (~8)
+    ops_to = 32 * 64 * 6 + 32 * 30
+    ops_from = 2 * ops_to + 32 * 64 * 8
+    r.close()
+    return {"workload": "2^17 integers below P, 32 primes of 60-62 bits",
+            "to_residues_us": round(ms_to * 1e3, 1), "from_residues_us": round(ms_from * 1e3, 1),
+            "to_melem_s": round(n / (ms_to * 1e-3) / 1e6, 1),
+            "from_melem_s": round(n / (ms_from * 1e-3) / 1e6, 1),
+            "roofline": {"bound": "alu", "unit": "T int-ops/s", "peak": round(ISSUE_PEAK / 1e12, 2),
+                         "achieved_to": round(n * ops_to / (ms_to * 1e-3) / 1e12, 2),
+                         "achieved_from": round(n * ops_from / (ms_from * 1e-3) / 1e12, 2),
+                         "frac_to": round(n * ops_to / (ms_to * 1e-3) / ISSUE_PEAK, 3),
+                         "frac_from": round(n * ops_from / (ms_from * 1e-3) / ISSUE_PEAK, 3)}}
+
+
+def _product(xs):
+    p = 1
+    for x in xs:
+        p *= x
+    return p
+
+
 def extra_serving(mg, jobs_count):
     """Poisson stream of mixed jobs through the serving loop at 0.5x and 0.8x
     of the measured capacity."""
@@ -650,6 +692,7 @@ def run_ours(args):
             "sweep_r16": extra_sweep(mg, stream),
             "ntt": extra_ntt(mg, stream, peak),
             "dot_lazy": extra_dot(mg, stream, peak),
+            "rns_convert": extra_rns(mg, stream),
             "serving": extra_serving(mg, args.serving_jobs),
         }
 

@@ -163,17 +163,26 @@ def _less_than_limbs(x: np.ndarray, n: np.ndarray) -> np.ndarray:
 
 
 def uniform_limb_residues(N: int, k: int, count: int, seed: int) -> np.ndarray:
-    """``count`` residues uniform in [0, N) as a (count, k) uint32 limb array."""
+    """``count`` residues uniform in [0, N) as a (count, k) uint32 limb array.
+
+    Draws the limbs N occupies, the top one uniform in [0, top limb of N] and
+    the others uniform, rejects values >= N (at least half are kept), and pads
+    with zero limbs up to k."""
     g = rng(seed)
-    n = limbs_of(N, k)
-    out = np.empty((count, k), dtype=np.uint32)
+    kk = max(1, (N.bit_length() + 31) // 32)
+    if kk > k:
+        raise ValueError("N does not fit in k limbs")
+    n = limbs_of(N, kk)
+    top = int(n[kk - 1])
+    out = np.zeros((count, k), dtype=np.uint32)
     filled = 0
     while filled < count:
         want = 2 * (count - filled) + 64
-        x = g.integers(0, 1 << 32, size=(want, k), dtype=np.uint64).astype(np.uint32)
+        x = g.integers(0, 1 << 32, size=(want, kk), dtype=np.uint64).astype(np.uint32)
+        x[:, kk - 1] = g.integers(0, top + 1, size=want, dtype=np.uint64).astype(np.uint32)
         x = x[_less_than_limbs(x, n)]
         take = min(len(x), count - filled)
-        out[filled:filled + take] = x[:take]
+        out[filled:filled + take, :kk] = x[:take]
         filled += take
     return out
 
