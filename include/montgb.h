@@ -170,6 +170,93 @@ int mont_to_domain(mont_ctx_t ctx, const void* x, void* out, size_t n, void* str
  */
 int mont_from_domain(mont_ctx_t ctx, const void* y, void* out, size_t n, void* stream);
 
+/* --------------------------------------------------- host-buffer pipeline */
+/*
+ * The element-wise operations above on vectors that live in HOST memory.
+ * The paper has no counterpart (it states the reductions, not where their
+ * operands live); this is the library's transfer layer.
+ *
+ * A pipe owns one device staging buffer, cut into MONT_PIPE_SLOTS fixed
+ * slots, and three CUDA streams.  mont_pipe_run splits the element range
+ * into chunks and, for chunk c in slot c mod MONT_PIPE_SLOTS, copies the
+ * chunk of every distinct input to the device, runs every operation on it
+ * with the element-wise kernels above and copies every result chunk back, so
+ * that host-to-device copies, kernels and device-to-host copies of
+ * consecutive chunks overlap.  An input that several operations name (the
+ * same host address, element size and length) is copied once per chunk.
+ * The results are bit-identical to the device-pointer entry points.
+ */
+#define MONT_PIPE_SLOTS    3    /* chunks in flight                              */
+#define MONT_PIPE_MAX_OPS  256  /* operations in one mont_pipe_run               */
+#define MONT_PIPE_MIN_CHUNK 256 /* smallest chunk, in elements                   */
+
+/* The operation of one mont_host_op. */
+#define MONT_OP_MUL         0   /* out = reduce(a b)          (mont_mul)          */
+#define MONT_OP_REDC        1   /* out = reduce(a), a double-width (mont_redc)    */
+#define MONT_OP_TO_DOMAIN   2   /* out = to(a)                (mont_to_domain)    */
+#define MONT_OP_FROM_DOMAIN 3   /* out = from(a)              (mont_from_domain)  */
+
+typedef struct mont_host_op {
+  mont_ctx_t ctx;   /* any ctx (word or multi-limb); fixes the element size e   */
+  int op;           /* MONT_OP_*                                                  */
+  const void* a;    /* HOST pointer: n elements of e bytes (2e for MONT_OP_REDC)  */
+  const void* b;    /* HOST pointer: n elements of e bytes (MONT_OP_MUL only)     */
+  void* out;        /* HOST pointer: n elements of e bytes                        */
+  size_t n;         /* elements; 0 skips the operation                            */
+} mont_host_op;
+
+typedef struct mont_pipe* mont_pipe_t;
+
+/*
+ * mont_pipe_create -- a pipe on the current device with `staging_bytes` of
+ * device memory (split into MONT_PIPE_SLOTS equal slots).  MONT_EINVAL if
+ * out is NULL or staging_bytes < MONT_PIPE_SLOTS * 64 KiB; MONT_ENOMEM if the
+ * staging memory cannot be allocated; MONT_ECUDA if a stream or event
+ * cannot be created.
+ */
+int mont_pipe_create(mont_pipe_t* out, size_t staging_bytes);
+
+/*
+ * mont_pipe_run -- run `count` operations on host vectors.
+ *
+ * Ordering: the pipe's work starts after all work enqueued on `stream`
+ * before the call, and `stream` waits for the last result copy, so a later
+ * call or mont_sync(stream) sees every result in host memory.  The call
+ * itself only enqueues (it returns before the copies finish); the host
+ * buffers must stay valid, and the inputs unmodified, until `stream` has
+ * passed that point.  Calls on one pipe are serialised by an internal lock;
+ * back-to-back calls on one pipe reuse its slots safely without a
+ * synchronisation in between.
+ *
+ * Host memory: page-locked (pinned) memory gives overlapped copies in both
+ * directions; pageable memory gives the same results but copies that do not
+ * overlap.
+ *
+ * Chunk C: the largest multiple of MONT_PIPE_MIN_CHUNK elements for which one
+ * chunk of every distinct input and every output fits one slot, capped so
+ * that one chunk of the widest vector is at most 16 MiB.
+ *
+ * Errors (nothing is enqueued): MONT_EINVAL if pipe or ops is NULL, count is
+ * outside 0..MONT_PIPE_MAX_OPS, an operation has a NULL ctx or pointer or an
+ * unknown op code; MONT_EINVAL too if an output range
+ * overlaps an input range or another output range in host memory, or if the
+ * current device is not the pipe's; MONT_ENOMEM if one slot cannot hold
+ * MONT_PIPE_MIN_CHUNK elements of every vector.  MONT_ECUDA if enqueueing
+ * fails part-way (`stream` still waits for what was enqueued).  count = 0 is
+ * a no-op.
+ */
+int mont_pipe_run(mont_pipe_t pipe, const mont_host_op* ops, int count, void* stream);
+
+/* Chunk (elements) and number of distinct inputs mont_pipe_run would use for
+ * these operations (no work enqueued); errors as mont_pipe_run's argument
+ * checks. */
+int mont_pipe_plan(mont_pipe_t pipe, const mont_host_op* ops, int count, size_t* chunk,
+                   int* distinct_inputs);
+
+/* Wait for the pipe's streams, then free its staging memory, streams and
+ * events.  NULL is accepted. */
+int mont_pipe_destroy(mont_pipe_t pipe);
+
 /* -------------------------------------------- fixed multipliers (Plantard) */
 /*
  * Section 3.2: Plantard's reduction lets a fixed multiplier b be prepared once

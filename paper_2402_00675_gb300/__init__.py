@@ -84,6 +84,19 @@ class MontLaunchShape(ctypes.Structure):
 MONT_JOB_MODMUL = 0
 MONT_JOB_SWEEP = 1
 
+MONT_PIPE_SLOTS = 3
+MONT_PIPE_MAX_OPS = 256
+MONT_PIPE_MIN_CHUNK = 256
+MONT_OP_MUL = 0
+MONT_OP_REDC = 1
+MONT_OP_TO_DOMAIN = 2
+MONT_OP_FROM_DOMAIN = 3
+
+
+class MontHostOp(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("op", ctypes.c_int), ("a", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_size_t)]
+
 
 class MontJob(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ctx", ctypes.c_void_p), ("a", ctypes.c_void_p),
@@ -186,6 +199,11 @@ def _declare(L):
         "mont_rns_to_residues": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_rns_from_residues": (_int, [_vp, _vp, _vp, _sz, _vp]),
         "mont_rns_destroy": (_int, [_vp]),
+        "mont_pipe_create": (_int, [_c.POINTER(_vp), _sz]),
+        "mont_pipe_run": (_int, [_vp, _c.POINTER(MontHostOp), _int, _vp]),
+        "mont_pipe_plan": (_int, [_vp, _c.POINTER(MontHostOp), _int, _c.POINTER(_sz),
+                                  _c.POINTER(_int)]),
+        "mont_pipe_destroy": (_int, [_vp]),
         "mont_strerror": (_c.c_char_p, [_int]),
         "mont_last_cuda_error": (_int, []),
         "mont_sync": (_int, [_vp]),
@@ -590,6 +608,76 @@ def mont_server_create(mem_budget_bytes: int, slots: int = 4, job_timeout_ms: in
 
 def mont_server_destroy(server: Server) -> None:
     server.close()
+
+
+class Pipe:
+    """A mont_pipe_t: element-wise operations on vectors in host memory.
+
+    ``ops`` is a sequence of ``(ctx, op, a, b, out)`` or ``(ctx, op, a, b, out, n)``
+    tuples: ``op`` a ``MONT_OP_*`` code, ``a``/``b``/``out`` CPU tensors, numpy
+    arrays or host addresses (``b`` None unless ``op`` is ``MONT_OP_MUL``), ``n``
+    defaulting to the elements ``out`` holds.  The buffers must stay alive and
+    the inputs unchanged until the stream passes the run.
+    """
+
+    def __init__(self, staging_bytes: int = 256 << 20):
+        h = ctypes.c_void_p()
+        _check(lib().mont_pipe_create(ctypes.byref(h), staging_bytes), "mont_pipe_create")
+        self.handle = h.value
+
+    @staticmethod
+    def _ops(ops):
+        arr = (MontHostOp * max(len(ops), 1))()
+        for i, o in enumerate(ops):
+            ctx, code, a, b, out = o[:5]
+            if len(o) > 5:
+                n = o[5]
+            elif out is None:
+                n = 0
+            else:
+                nb = _nbytes(out) if hasattr(out, "numel") else out.nbytes
+                n = nb // ctx.elem_bytes
+            hp = [None if x is None else _host_ptr(x) for x in (a, b, out)]
+            arr[i] = MontHostOp(ctx=ctx.handle, op=code, a=hp[0], b=hp[1], out=hp[2], n=n)
+        return arr
+
+    def run(self, ops, stream=None) -> None:
+        _check(lib().mont_pipe_run(self.handle, self._ops(ops), len(ops), _stream(stream)),
+               "mont_pipe_run")
+
+    def plan(self, ops) -> tuple[int, int]:
+        """(chunk in elements, distinct inputs) a run of ``ops`` would use."""
+        chunk, distinct = ctypes.c_size_t(), ctypes.c_int()
+        _check(lib().mont_pipe_plan(self.handle, self._ops(ops), len(ops), ctypes.byref(chunk),
+                                    ctypes.byref(distinct)), "mont_pipe_plan")
+        return chunk.value, distinct.value
+
+    def close(self):
+        if self.handle:
+            lib().mont_pipe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mont_pipe_create(staging_bytes: int = 256 << 20) -> Pipe:
+    return Pipe(staging_bytes)
+
+
+def mont_pipe_run(pipe: Pipe, ops, stream=None) -> None:
+    pipe.run(ops, stream)
+
+
+def mont_pipe_plan(pipe: Pipe, ops) -> tuple[int, int]:
+    return pipe.plan(ops)
+
+
+def mont_pipe_destroy(pipe: Pipe) -> None:
+    pipe.close()
 
 
 def mont_probe_int_rate(kind: int, iters: int = 4096, stream=None) -> float:

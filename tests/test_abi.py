@@ -200,3 +200,9 @@ def test_server_and_device_calls_fail_cleanly_without_gpu(L):
     assert st in (mg.MONT_ECUDA, mg.MONT_ENOMEM)
     assert L.mont_server_create(ctypes.byref(h), 1 << 20, 0, 0) == mg.MONT_EINVAL
     assert L.mont_server_destroy(None) == mg.MONT_OK
+    assert L.mont_pipe_create(ctypes.byref(h), 1 << 20) in (mg.MONT_ECUDA, mg.MONT_ENOMEM)
+    assert L.mont_pipe_create(ctypes.byref(h), 1000) == mg.MONT_EINVAL
+    assert L.mont_pipe_create(None, 1 << 20) == mg.MONT_EINVAL
+    assert L.mont_pipe_run(None, None, 0, None) == mg.MONT_EINVAL
+    assert L.mont_pipe_plan(None, None, 0, None, None) == mg.MONT_EINVAL
+    assert L.mont_pipe_destroy(None) == mg.MONT_OK
