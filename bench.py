@@ -330,6 +330,49 @@ def extra_cios(mg, stream, peak):
     return out
 
 
+def extra_limb_variants(mg, stream, peak):
+    """Algorithms 1-4 at 256 and 1024 bits (n = 32k: R = 2^{32k} for
+    Algorithm 1, 2^{64k} for Algorithms 2-4), random odd N at each variant's
+    largest size class, operands uniform in the variant's output range."""
+    import torch
+    out = {}
+    names = {1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
+    for bits, count in ((256, 1 << 21), (1024, 1 << 17)):
+        k = bits // 32
+        L = mg.lib()
+        sp = stream.cuda_stream
+        for variant in (1, 2, 3, 4):
+            top_bits = {1: bits - 1, 2: bits - 1, 3: bits - 1, 4: bits - 2}[variant]
+            N = sy.random_odd_modulus(top_bits, seed=4 + variant)
+            log2R = 2 * bits if variant >= 2 else bits
+            ctx = mg.mont_ctx_create(N, log2R, variant, alpha=1, n_limbs=k)
+            a = sy.uniform_limb_residues(N, k, count, seed=40 + variant)
+            b = sy.uniform_limb_residues(N, k, count, seed=80 + variant)
+            if variant != 2:   # signed variants: centre the residues (x - N for x > N/2)
+                a, b = (sy.centred_limb_residues(N, x) for x in (a, b))
+            da = torch.from_numpy(a.reshape(-1)).cuda()
+            db = torch.from_numpy(b.reshape(-1)).cuda()
+            o = torch.empty_like(da)
+            f = lambda: L.mont_mul(ctx.handle, da.data_ptr(), db.data_ptr(), o.data_ptr(), count, sp)
+            for _ in range(5):
+                f()
+            ms = _events_ms(f, 20, stream)
+            # limb products as the kernel forms them: T = a b (k^2), then
+            # Algorithm 1: m low half (k(k+1)/2) and m N (k^2);
+            # Algorithms 2-4: m = T N^{-1} mod 2^{64k} (k(2k+1)) and q N ((k+1) k)
+            per = 2.5 * k * k + k / 2 if variant == 1 else 4 * k * k + 2 * k
+            ach = per * count / (ms * 1e-3)
+            out[f"{bits}b_{names[variant]}"] = {
+                "pairs": count, "gmodmul_s": round(count / (ms * 1e-3) / 1e9, 3),
+                "us": round(ms * 1e3, 2),
+                "roofline": {"bound": "alu", "achieved": round(ach / 1e12, 3),
+                             "peak": round(LIMB_PRODUCT_PEAK / 1e12, 3),
+                             "unit": "T limb-products/s (32x32->64, lo+hi)",
+                             "frac": round(ach / LIMB_PRODUCT_PEAK, 3),
+                             "hbm_frac": round(12 * k * count / (ms * 1e-3) / 1e9 / peak, 3)}}
+    return out
+
+
 def extra_sweep(mg, stream):
     """R = 2^16, every odd N in [3, 4095]; each algorithm on its own domain,
     and on REDC's domain 0 <= T < RN."""
@@ -666,6 +709,7 @@ def run_ours(args):
             "redc32_2p20": extra_redc32(mg, stream, peak),
             "rns64_batched": extra_rns64(mg, stream, peak),
             "cios": extra_cios(mg, stream, peak),
+            "limb_variants": extra_limb_variants(mg, stream, peak),
             "sweep_r16": extra_sweep(mg, stream),
             "ntt": extra_ntt(mg, stream, peak),
             "dot_lazy": extra_dot(mg, stream, peak),

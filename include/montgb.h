@@ -84,7 +84,8 @@ typedef struct mont_ctx* mont_ctx_t;  /* opaque; owned by the library */
  *   N_limbs  host pointer to n_limbs little-endian 32-bit limbs of the odd
  *            modulus N >= 3.  Upper limbs may be zero.
  *   n_limbs  1 -> 32-bit word kernels, 2 -> 64-bit word kernels,
- *            8..MONT_MAX_LIMBS -> multi-limb kernels (REDC only).
+ *            4, 8, 12, 16, 32 or 64 -> multi-limb kernels (every variant;
+ *            signed elements are k-limb two's complement integers).
  *   log2R    R = 2^log2R.  Must be 32*n_limbs for MONT_REDC and MONT_SIGNED,
  *            and 64*n_limbs (the paper's R = 2^{2n} with n the word size) for
  *            the three Plantard variants.

@@ -296,6 +296,13 @@ int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y,
     const uintptr_t yo = reinterpret_cast<uintptr_t>(y);
     if (yo != oo && yo < oo + n * esize && oo < yo + n * esize) return MONT_EINVAL;
   }
+  if (ctx->variant != MONT_REDC) {   // Algorithms 1-4 (limb_variants.cu)
+    const int v16 = aligned(x, 16) && aligned(out, 16) && (!y || aligned(y, 16)) ? 1 : 0;
+    return cuda_status(launch_limb_variant(k, mode, ctx->limbv, static_cast<const uint32_t*>(x),
+                                           static_cast<const uint32_t*>(y),
+                                           static_cast<uint32_t*>(out), n,
+                                           static_cast<cudaStream_t>(stream), v16));
+  }
   LaunchShape shape = tuned_shape(ctx->width, ctx->variant, static_cast<int>(mode));
   int team = shape.team > 0 ? shape.team : default_team(k);
   if (!team_supported(k, team)) team = default_team(k);

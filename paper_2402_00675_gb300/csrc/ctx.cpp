@@ -149,7 +149,6 @@ extern "C" int mont_ctx_create(mont_ctx_t* out, const uint32_t* N_limbs, int n_l
   if (variant < MONT_REDC || variant > MONT_SIGNED_PLANTARD2) return MONT_EINVAL;
   const bool word = (n_limbs == 1 || n_limbs == 2);
   if (!word && !is_supported_multilimb(n_limbs)) return MONT_EINVAL;
-  if (!word && variant != MONT_REDC) return MONT_EINVAL;
   const bool plantard = variant >= MONT_PLANTARD;
   const int want_log2R = plantard ? 64 * n_limbs : 32 * n_limbs;
   if (log2R != want_log2R) return MONT_EINVAL;
@@ -238,6 +237,16 @@ extern "C" int mont_ctx_create(mont_ctx_t* out, const uint32_t* N_limbs, int n_l
       k.N[i] = N[i];
       k.r2[i] = c->r2_mod_n[i];
     }
+    auto& v = c->limbv;
+    v.variant = variant;
+    v.alpha = c->alpha;
+    // half = (N - 1) / 2 = N >> 1 (N odd), shifted limb by limb
+    for (int i = 0; i < n_limbs; ++i) {
+      v.N[i] = N[i];
+      v.dom[i] = c->domain_r2[i];
+      v.half[i] = (N[i] >> 1) | (i + 1 < n_limbs ? (N[i + 1] << 31) : 0u);
+    }
+    for (size_t i = 0; i < LR; ++i) v.ninv[i] = c->ninv[i];
   }
   *out = c;
   return MONT_OK;

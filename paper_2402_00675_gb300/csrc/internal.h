@@ -46,6 +46,17 @@ struct LimbConst {
   uint32_t r2[MONT_MAX_LIMBS];  // R^2 mod N
 };
 
+// Constants of one modulus for the multi-limb kernels of Algorithms 1-4
+// (R = 2^{32k} for Algorithm 1, 2^{64k} for the Plantard family).
+struct LimbVarConst {
+  int variant;
+  int alpha;
+  uint32_t N[MONT_MAX_LIMBS];
+  uint32_t ninv[2 * MONT_MAX_LIMBS];  // N^{-1} mod R: k limbs (Algorithm 1) or 2k (Algorithms 2-4)
+  uint32_t dom[MONT_MAX_LIMBS];       // mont_to_domain constant, two's complement for signed variants
+  uint32_t half[MONT_MAX_LIMBS];      // (N - 1) / 2
+};
+
 // Launch shape of an element-wise kernel.
 struct LaunchShape {
   int threads = 256;        // threads per block
@@ -65,6 +76,11 @@ cudaError_t launch_word32(int variant, Mode mode, const WordConst32& c, const vo
 cudaError_t launch_word64(int variant, Mode mode, const WordConst64& c, const void* x,
                           const void* y, void* out, size_t n, cudaStream_t s,
                           const LaunchShape& shape);
+
+// Multi-limb Algorithms 1-4 (limb_variants.cu); k in {4, 8, 12, 16, 32, 64}.
+cudaError_t launch_limb_variant(int k, Mode mode, const LimbVarConst& c, const uint32_t* x,
+                                const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s,
+                                int vec16);
 
 // Number of SMs of the current device (cached per device).
 int device_sm_count();
@@ -86,6 +102,7 @@ struct mont_ctx {
   montgb::WordConst32 w32{};
   montgb::WordConst64 w64{};
   montgb::LimbConst limb{};
+  montgb::LimbVarConst limbv{};
 };
 
 namespace montgb {

@@ -1,0 +1,320 @@
+// Algorithms 1-4 at multi-limb widths.
+//
+// The paper states Algorithm 1 for R = 2^n and the Plantard family
+// (Algorithms 2-4) for R = 2^{2n}, for any word size n.  For a modulus of k
+// 32-bit limbs the library takes n = 32k: Algorithm 1 works modulo
+// R = 2^{32k}, Algorithms 2-4 modulo R = 2^{64k}.  Signed elements are k-limb
+// two's complement integers.  Every step is exact limb arithmetic:
+//
+//   Algorithm 1  m = (T mod R) N^{-1} mods R                 (low k limbs)
+//                r = (T >> n) - ((m N) >> n)                  in (-N, N)
+//   Algorithm 2  m = T N^{-1} mod 2^{2n}                      (low 2k limbs)
+//                r = (((m >> n) + 1) N) >> n                  in [0, N)
+//   Algorithm 3  m = (int_{2n})(T N^{-1}),  q = (m + 2^{n-1}) >> n,
+//                r = (q N + 2^{n-1}) >> n                     mods N
+//   Algorithm 4  m = (int_{2n})(T N^{-1}),
+//                r = (((m >> n) + 2^alpha) N) >> n            mods N (alpha >= 1)
+//
+// Shifts of signed values are arithmetic.  A product with a signed factor
+// is formed as the unsigned product of the two's complement limbs, then
+// corrected: a factor x < 0 stands for x + 2^{32j} (j its limbs), so the
+// other factor times 2^{32j} is subtracted from the limbs it reaches.
+//
+// One thread per element, grid-stride.  Up to k = 16 the loops are fully
+// unrolled and the arrays live in registers; at k = 32 and 64 they live in
+// local memory.  The variant and the operation are uniform run-time
+// branches: one kernel per limb count.
+#include "internal.h"
+
+namespace montgb {
+namespace {
+
+constexpr int unroll_for(int k) { return k <= 16 ? 128 : 1; }
+
+// out[0, KA+KB) = a[0, KA) * b[0, KB), unsigned.
+template <int K, int KA, int KB>
+__device__ __forceinline__ void mul_full(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  constexpr int U = unroll_for(K);
+#pragma unroll U
+  for (int i = 0; i < KA + KB; ++i) out[i] = 0;
+#pragma unroll U
+  for (int i = 0; i < KA; ++i) {
+    uint32_t carry = 0;
+#pragma unroll U
+    for (int j = 0; j < KB; ++j) {
+      const uint64_t t = static_cast<uint64_t>(a[i]) * b[j] + out[i + j] + carry;
+      out[i + j] = static_cast<uint32_t>(t);
+      carry = static_cast<uint32_t>(t >> 32);
+    }
+    out[i + KB] = carry;
+  }
+}
+
+// out[0, M) = (a[0, KA) * b[0, KB)) mod 2^{32M}, unsigned.
+template <int K, int KA, int KB, int M>
+__device__ __forceinline__ void mul_low(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  constexpr int U = unroll_for(K);
+#pragma unroll U
+  for (int i = 0; i < M; ++i) out[i] = 0;
+#pragma unroll U
+  for (int i = 0; i < KA; ++i) {
+    if (i >= M) break;
+    uint32_t carry = 0;
+#pragma unroll U
+    for (int j = 0; j < KB; ++j) {
+      if (i + j >= M) break;
+      const uint64_t t = static_cast<uint64_t>(a[i]) * b[j] + out[i + j] + carry;
+      out[i + j] = static_cast<uint32_t>(t);
+      carry = static_cast<uint32_t>(t >> 32);
+    }
+    if (i + KB < M) out[i + KB] = carry;
+  }
+}
+
+// x[0, L) -= (y[0, L) & mask), modulo 2^{32L}.
+template <int K, int L>
+__device__ __forceinline__ void sub_masked(uint32_t* x, const uint32_t* y, uint32_t mask) {
+  constexpr int U = unroll_for(K);
+  uint32_t borrow = 0;
+#pragma unroll U
+  for (int i = 0; i < L; ++i) {
+    const uint64_t d = static_cast<uint64_t>(x[i]) - (y[i] & mask) - borrow;
+    x[i] = static_cast<uint32_t>(d);
+    borrow = static_cast<uint32_t>(d >> 32) & 1u;
+  }
+}
+
+// x[0, L) += (y[0, L) & mask), modulo 2^{32L}.
+template <int K, int L>
+__device__ __forceinline__ void add_masked(uint32_t* x, const uint32_t* y, uint32_t mask) {
+  constexpr int U = unroll_for(K);
+  uint32_t carry = 0;
+#pragma unroll U
+  for (int i = 0; i < L; ++i) {
+    const uint64_t s = static_cast<uint64_t>(x[i]) + (y[i] & mask) + carry;
+    x[i] = static_cast<uint32_t>(s);
+    carry = static_cast<uint32_t>(s >> 32);
+  }
+}
+
+// x[0, L) += 2^bit, modulo 2^{32L} (bit < 32 L).
+template <int K, int L>
+__device__ __forceinline__ void add_pow2(uint32_t* x, int bit) {
+  constexpr int U = unroll_for(K);
+  const int limb = bit >> 5;
+  uint32_t carry = 0;
+#pragma unroll U
+  for (int i = 0; i < L; ++i) {
+    const uint32_t add = (i == limb ? (1u << (bit & 31)) : 0u) + carry;
+    const uint32_t s = x[i] + add;
+    carry = s < add ? 1u : 0u;
+    x[i] = s;
+  }
+}
+
+__device__ __forceinline__ uint32_t sign_mask(uint32_t top) { return 0u - (top >> 31); }
+
+// Algorithm 1 at R = 2^{32K}: T (2K limbs, two's complement) -> r (K limbs).
+template <int K>
+__device__ __forceinline__ void sig_redc(const uint32_t* T, const LimbVarConst& c, uint32_t* r) {
+  constexpr int U = unroll_for(K);
+  uint32_t m[K];
+  mul_low<K, K, K, K>(T, c.ninv, m);            // m = (T mod R) N^{-1} mod R; signed view = mods R
+  uint32_t P[2 * K];
+  mul_full<K, K, K>(m, c.N, P);                 // (m mod R) N
+#pragma unroll U
+  for (int i = 0; i < K; ++i) r[i] = T[K + i];  // T >> n (the high limbs, signed)
+  sub_masked<K, K>(r, P + K, 0xFFFFFFFFu);      // - ((m mod R) N >> n)
+  add_masked<K, K>(r, c.N, sign_mask(m[K - 1]));  // m < 0: (m N) >> n = ((m mod R) N >> n) - N
+}
+
+// m = T N^{-1} mod 2^{64K} (low 2K limbs) for the Plantard family.
+template <int K>
+__device__ __forceinline__ void plantard_m(const uint32_t* T, const LimbVarConst& c, uint32_t* m) {
+  mul_low<K, 2 * K, 2 * K, 2 * K>(T, c.ninv, m);
+}
+
+// r = (q N) >> n with q signed of K+1 limbs, plus 2^{n-1} before the shift
+// when round_half is set.  The product is formed on 2K+1 limbs.
+template <int K>
+__device__ __forceinline__ void shifted_product(const uint32_t* q, const LimbVarConst& c,
+                                                bool round_half, uint32_t* r) {
+  constexpr int U = unroll_for(K);
+  uint32_t P[2 * K + 1];
+  mul_full<K, K + 1, K>(q, c.N, P);
+  // q < 0 stands for q + 2^{32(K+1)}: remove N 2^{32(K+1)} from limbs K+1..2K
+  sub_masked<K, K>(P + K + 1, c.N, sign_mask(q[K]));
+  if (round_half) add_pow2<K, 2 * K + 1>(P, 32 * K - 1);
+#pragma unroll U
+  for (int i = 0; i < K; ++i) r[i] = P[K + i];
+}
+
+// Algorithm 2 at R = 2^{64K}.
+template <int K>
+__device__ __forceinline__ void p_redc(const uint32_t* T, const LimbVarConst& c, uint32_t* r) {
+  constexpr int U = unroll_for(K);
+  uint32_t m[2 * K];
+  plantard_m<K>(T, c, m);
+  uint32_t q[K + 1];                            // (m >> n) + 1, unsigned
+  uint32_t carry = 1;
+#pragma unroll U
+  for (int i = 0; i < K; ++i) {
+    const uint32_t s = m[K + i] + carry;
+    carry = s < carry ? 1u : 0u;
+    q[i] = s;
+  }
+  q[K] = carry;
+  shifted_product<K>(q, c, false, r);           // q >= 0: no sign correction applies
+}
+
+// Algorithms 3 and 4 at R = 2^{64K}.
+template <int K>
+__device__ __forceinline__ void sig_p_redc(const uint32_t* T, const LimbVarConst& c, uint32_t* r) {
+  constexpr int U = unroll_for(K);
+  uint32_t m[2 * K];
+  plantard_m<K>(T, c, m);                       // two's complement view = (int_{2n})(T N^{-1})
+  uint32_t q[K + 1];
+  if (c.variant == MONT_SIGNED_PLANTARD) {
+    // q = (m + 2^{n-1}) >> n on 2K+1 limbs: add 2^31 to limb K-1, carry upward
+    uint32_t carry = (m[K - 1] + 0x80000000u) < m[K - 1] ? 1u : 0u;
+#pragma unroll U
+    for (int i = 0; i < K; ++i) {
+      const uint32_t s = m[K + i] + carry;
+      carry = s < carry ? 1u : 0u;
+      q[i] = s;
+    }
+    q[K] = sign_mask(m[2 * K - 1]) + carry;
+    shifted_product<K>(q, c, true, r);
+  } else {
+    // q = (m >> n) + 2^alpha on K+1 limbs
+#pragma unroll U
+    for (int i = 0; i < K; ++i) q[i] = m[K + i];
+    q[K] = sign_mask(m[2 * K - 1]);
+    add_pow2<K, K + 1>(q, c.alpha);
+    shifted_product<K>(q, c, false, r);
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void load_limbs(const uint32_t* p, uint32_t* v, int vec16) {
+  constexpr int U = unroll_for(C / 2);
+  if (C % 4 == 0 && vec16) {
+#pragma unroll U
+    for (int q = 0; q < C / 4; ++q) {
+      const uint4 u = reinterpret_cast<const uint4*>(p)[q];
+      v[4 * q] = u.x;
+      v[4 * q + 1] = u.y;
+      v[4 * q + 2] = u.z;
+      v[4 * q + 3] = u.w;
+    }
+  } else {
+#pragma unroll U
+    for (int i = 0; i < C; ++i) v[i] = p[i];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void store_limbs(uint32_t* p, const uint32_t* v, int vec16) {
+  constexpr int U = unroll_for(K);
+  if (K % 4 == 0 && vec16) {
+#pragma unroll U
+    for (int q = 0; q < K / 4; ++q)
+      reinterpret_cast<uint4*>(p)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll U
+    for (int i = 0; i < K; ++i) p[i] = v[i];
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) limb_variant_kernel(const uint32_t* __restrict__ x,
+                                                           const uint32_t* __restrict__ y,
+                                                           uint32_t* __restrict__ out, size_t n,
+                                                           int mode, int vec16,
+                                                           const LimbVarConst c) {
+  constexpr int U = unroll_for(K);
+  const bool is_signed = c.variant != MONT_PLANTARD;
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += stride) {
+    uint32_t T[2 * K];
+    if (mode == static_cast<int>(Mode::kRedc)) {
+      load_limbs<2 * K>(x + e * 2 * K, T, vec16);
+    } else {
+      uint32_t a[K];
+      load_limbs<K>(x + e * K, a, vec16);
+      if (mode == static_cast<int>(Mode::kFromDomain)) {
+        const uint32_t ext = is_signed ? sign_mask(a[K - 1]) : 0u;
+#pragma unroll U
+        for (int i = 0; i < K; ++i) {
+          T[i] = a[i];
+          T[K + i] = ext;
+        }
+      } else {
+        uint32_t b[K];
+        if (mode == static_cast<int>(Mode::kMul)) {
+          load_limbs<K>(y + e * K, b, vec16);
+        } else {
+#pragma unroll U
+          for (int i = 0; i < K; ++i) b[i] = c.dom[i];
+        }
+        mul_full<K, K, K>(a, b, T);
+        if (is_signed) {                        // T mod 2^{64K} of the signed product
+          sub_masked<K, K>(T + K, b, sign_mask(a[K - 1]));
+          sub_masked<K, K>(T + K, a, sign_mask(b[K - 1]));
+        }
+      }
+    }
+    uint32_t r[K];
+    if (c.variant == MONT_SIGNED) {
+      sig_redc<K>(T, c, r);
+      if (mode == static_cast<int>(Mode::kFromDomain)) {
+        // (-N, N) -> mods N: r > (N-1)/2 gives r - N, r < -(N-1)/2 gives r + N
+        uint32_t t[K];
+#pragma unroll U
+        for (int i = 0; i < K; ++i) t[i] = c.half[i];
+        sub_masked<K, K>(t, r, 0xFFFFFFFFu);    // (N-1)/2 - r
+        const uint32_t above = sign_mask(t[K - 1]);
+#pragma unroll U
+        for (int i = 0; i < K; ++i) t[i] = r[i];
+        add_masked<K, K>(t, c.half, 0xFFFFFFFFu);   // r + (N-1)/2
+        const uint32_t below = sign_mask(t[K - 1]);
+        sub_masked<K, K>(r, c.N, above);
+        add_masked<K, K>(r, c.N, below);
+      }
+    } else if (c.variant == MONT_PLANTARD) {
+      p_redc<K>(T, c, r);
+    } else {
+      sig_p_redc<K>(T, c, r);
+    }
+    store_limbs<K>(out + e * K, r, vec16);
+  }
+}
+
+template <int K>
+cudaError_t launch_k(Mode mode, const LimbVarConst& c, const uint32_t* x, const uint32_t* y,
+                     uint32_t* o, size_t n, cudaStream_t s, int vec16) {
+  const void* kern = reinterpret_cast<const void*>(limb_variant_kernel<K>);
+  const size_t want = (n + 127) / 128;
+  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(kern, 128);
+  limb_variant_kernel<K><<<static_cast<unsigned>(want < cap ? want : cap), 128, 0, s>>>(
+      x, y, o, n, static_cast<int>(mode), vec16, c);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_limb_variant(int k, Mode mode, const LimbVarConst& c, const uint32_t* x,
+                                const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s,
+                                int vec16) {
+  switch (k) {
+    case 4: return launch_k<4>(mode, c, x, y, o, n, s, vec16);
+    case 8: return launch_k<8>(mode, c, x, y, o, n, s, vec16);
+    case 12: return launch_k<12>(mode, c, x, y, o, n, s, vec16);
+    case 16: return launch_k<16>(mode, c, x, y, o, n, s, vec16);
+    case 32: return launch_k<32>(mode, c, x, y, o, n, s, vec16);
+    case 64: return launch_k<64>(mode, c, x, y, o, n, s, vec16);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace montgb

@@ -28,7 +28,8 @@ import numpy as np
 __all__ = [
     "rng", "uniform_residues", "centred_residues", "lift_unsigned", "is_probable_prime",
     "rns_primes", "log_uniform_lengths", "random_odd_modulus", "limbs_of",
-    "int_of_limbs", "uniform_limb_residues", "bounded_limb_residues", "Job", "serving_jobs",
+    "int_of_limbs", "uniform_limb_residues", "bounded_limb_residues", "centred_limb_residues",
+    "Job", "serving_jobs",
     "REDC32_N", "WORD32_MODULI", "ntt_prime", "primitive_2n_root",
 ]
 
@@ -184,6 +185,24 @@ def uniform_limb_residues(N: int, k: int, count: int, seed: int) -> np.ndarray:
         take = min(len(x), count - filled)
         out[filled:filled + take, :kk] = x[:take]
         filled += take
+    return out
+
+
+def centred_limb_residues(N: int, x: np.ndarray) -> np.ndarray:
+    """Residues ``x`` in [0, N) (a (count, k) limb array) moved to the centred
+    interval [-(N-1)/2, (N-1)/2], each stored as k-limb two's complement:
+    the rows above (N-1)/2 become x - N (mod 2^{32k})."""
+    count, k = x.shape
+    above = ~_less_than_limbs(x, limbs_of((N - 1) // 2 + 1, k))
+    n = limbs_of(N, k).astype(np.int64)
+    rows = x[above].astype(np.int64)
+    borrow = np.zeros(rows.shape[0], dtype=np.int64)
+    for j in range(k):
+        d = rows[:, j] - n[j] - borrow
+        borrow = (d < 0).astype(np.int64)
+        rows[:, j] = d + (borrow << 32)
+    out = x.copy()
+    out[above] = rows.astype(np.uint32)
     return out
 
 

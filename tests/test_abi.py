@@ -4,6 +4,7 @@ No test here launches a kernel; all run without a GPU."""
 
 import ctypes
 import glob
+import math
 import os
 import random
 import re
@@ -94,6 +95,19 @@ def test_multilimb_precompute_matches_oracle(L, k):
         assert _const(ctx, mg.MONT_CONST_NPRIME) == c.Nprime
         assert _const(ctx, mg.MONT_CONST_R2_MOD_N) == c.R2_mod_N
         assert _const(ctx, mg.MONT_CONST_R_MOD_N) == c.R_mod_N
+    # Algorithms 1-4 at k limbs: N^{-1} mod R at R = 2^{32k} or 2^{64k}, domain constant
+    for variant in (mg.MONT_SIGNED, mg.MONT_PLANTARD, mg.MONT_SIGNED_PLANTARD,
+                    mg.MONT_SIGNED_PLANTARD2):
+        log2R = 64 * k if variant in mg.PLANTARD_VARIANTS else 32 * k
+        N = rnd.randrange(1 << (32 * k - 3), 1 << (32 * k - 2)) | 1
+        ctx = mg.mont_ctx_create(N, log2R, variant, alpha=1, n_limbs=k)
+        assert _const(ctx, mg.MONT_CONST_NINV) == pow(N, -1, 1 << log2R)
+        r2 = pow(2, 2 * log2R, N)
+        dom = _const(ctx, mg.MONT_CONST_DOMAIN_R2)
+        if variant == mg.MONT_PLANTARD:
+            assert dom == r2
+        else:
+            assert dom == o.mods(r2, N) % (1 << (32 * k))    # two's complement in k limbs
     # a modulus with leading zero limbs is accepted too
     N = (1 << 100) + 3
     ctx = mg.mont_ctx_create(N, 32 * 8, 0, n_limbs=8)
@@ -126,8 +140,22 @@ def test_precondition_boundaries(L):
             mg.mont_ctx_create(*bad)
     with pytest.raises(mg.MontError):
         mg.mont_ctx_create(3329, 64, 0, n_limbs=1)          # log2R must be 32 n_limbs
+    # multi-limb moduli: each variant's condition on N at n = 32k (here n = 256)
+    # 2^n / phi = 2^{n-1} (sqrt(5) - 1): start from the integer square root
+    top = (math.isqrt(5 << 510) - (1 << 255)) | 1
+    while o.plantard_bound_ok(top + 2, 256):
+        top += 2
+    while not o.plantard_bound_ok(top, 256):
+        top -= 2
+    mg.mont_ctx_create(top, 512, mg.MONT_PLANTARD, n_limbs=8)
     with pytest.raises(mg.MontError):
-        mg.mont_ctx_create((1 << 255) + 1, 512, mg.MONT_PLANTARD, n_limbs=8)
+        mg.mont_ctx_create(top + 2, 512, mg.MONT_PLANTARD, n_limbs=8)
+    for variant, log2R, bound in ((mg.MONT_SIGNED, 256, 1 << 255),
+                                  (mg.MONT_SIGNED_PLANTARD, 512, 1 << 255),
+                                  (mg.MONT_SIGNED_PLANTARD2, 512, 1 << 254)):
+        mg.mont_ctx_create(bound - 1, log2R, variant, alpha=1, n_limbs=8)
+        with pytest.raises(mg.MontError):
+            mg.mont_ctx_create(bound + 1, log2R, variant, alpha=1, n_limbs=8)
     # REDC accepts N up to R - 1
     mg.mont_ctx_create((1 << 32) - 1, 32, 0)
     mg.mont_ctx_create((1 << 64) - 59, 64, 0)

@@ -76,3 +76,23 @@ def test_bounded_limb_residues():
     x = sy.bounded_limb_residues(N, 8, 5000, 3)
     assert x.shape == (5000, 8)
     assert all(sy.int_of_limbs(r) < N for r in x)
+
+
+def test_centred_limb_residues():
+    N = sy.random_odd_modulus(255, seed=5)
+    x = sy.uniform_limb_residues(N, 8, 4000, seed=3)
+    c = sy.centred_limb_residues(N, x)
+    half = (N - 1) // 2
+    signed = []
+    for xr, cr in zip(x, c):
+        v = sy.int_of_limbs(cr)
+        v = v - (1 << 256) if v >> 255 else v
+        assert (v - sy.int_of_limbs(xr)) % N == 0 and -half <= v <= half
+        signed.append(v)
+    assert 0.4 < sum(v < 0 for v in signed) / len(signed) < 0.6
+    # the ends of the interval map as specified
+    ends = np.stack([sy.limbs_of(half, 8), sy.limbs_of(half + 1, 8), sy.limbs_of(0, 8)])
+    got = sy.centred_limb_residues(N, ends)
+    assert sy.int_of_limbs(got[0]) == half
+    assert sy.int_of_limbs(got[1]) == (half + 1 - N) % (1 << 256)
+    assert sy.int_of_limbs(got[2]) == 0
