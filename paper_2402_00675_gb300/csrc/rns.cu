@@ -4,10 +4,17 @@
 // Big integer -> residues.  X mod p = sum_j X_j 2^{32 j} mod p over the 32-bit
 // limbs X_j.  With c_j = 2^{32 j} R mod p (R = 2^64), REDC(sum_j X_j c_j) =
 // X mod p: the sum of k products of a limb and a word stays below k 2^32 p <
-// p R, so it is accumulated exactly in 128 bits and reduced once.  One thread
-// per (element, modulus); consecutive threads take consecutive elements of one
-// modulus, so residue stores are coalesced, and a tile of 256 elements is
-// converted for every modulus before the next tile, so its limbs stay in L2.
+// p R, so it is accumulated exactly in 128 bits and reduced once.  The sums
+// form a product of an (elements x limbs) matrix and a (limbs x moduli)
+// matrix, so the kernel is tiled like one: a block converts 64 elements for
+// a group of up to 32 moduli, with the tile's limbs staged in shared memory
+// transposed ([limb][element], rows padded to 65 words, so that both the
+// coalesced staging writes and the per-limb reads are free of bank
+// conflicts) and the group's c_j as [limb][modulus].  Warp w takes moduli
+// 4w..4w+3 of the group and lane l elements l and l+32 of the tile: every
+// thread keeps 2 x 4 sums of four 32-bit words and spends one carry chain
+// (two mad.lo, two mad.hi, three addc) per limb product, reading one limb
+// per element and one broadcast 32-byte row of constants per limb.
 //
 // Residues -> big integer.  Mixed radix (Garner): X = sum_i v_i Pi_i with
 // Pi_i = p_0 ... p_{i-1} and v_i = (x_i - X_{<i}) Pi_i^{-1} mod p_i, where
@@ -29,33 +36,84 @@ namespace {
 
 constexpr int kRnsMaxModuli = 64;
 
+// a[0..3] += v c  (a 32-bit limb times a 64-bit word into a 128-bit sum)
+__device__ __forceinline__ void mac_limb_word(uint32_t (&a)[4], uint32_t v, uint64_t c) {
+  const uint32_t c0 = static_cast<uint32_t>(c), c1 = static_cast<uint32_t>(c >> 32);
+  asm("mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %5, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %6, %2;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      "mad.lo.cc.u32 %1, %4, %6, %1;\n\t"
+      "addc.cc.u32 %2, %2, 0;\n\t"
+      "addc.u32 %3, %3, 0;"
+      : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
+      : "r"(v), "r"(c0), "r"(c1));
+}
+
+constexpr int kToTile = 64;    // elements per tile
+constexpr int kToGroup = 32;   // moduli per block
+
 template <int K>
 __global__ void __launch_bounds__(256) rns_to_kernel(const uint32_t* __restrict__ X,
                                                      uint64_t* __restrict__ res, size_t n,
                                                      int count,
                                                      const WordConst64* __restrict__ mods,
                                                      const uint64_t* __restrict__ c) {
-  const size_t tiles = (n + 255) / 256;
-  const size_t total = tiles * static_cast<size_t>(count) * 256;
-  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
-       q += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const size_t t = q % 256;
-    const size_t rest = q / 256;
-    const int i = static_cast<int>(rest % count);
-    const size_t e = (rest / count) * 256 + t;
-    if (e >= n) continue;
-    const uint4* x = reinterpret_cast<const uint4*>(X + e * K);
-    const uint64_t* ci = c + static_cast<size_t>(i) * K;
-    u128 acc = 0;
-#pragma unroll
-    for (int j = 0; j < K / 4; ++j) {
-      const uint4 v = x[j];
-      acc += static_cast<u128>(v.x) * __ldg(ci + 4 * j);
-      acc += static_cast<u128>(v.y) * __ldg(ci + 4 * j + 1);
-      acc += static_cast<u128>(v.z) * __ldg(ci + 4 * j + 2);
-      acc += static_cast<u128>(v.w) * __ldg(ci + 4 * j + 3);
+  __shared__ uint32_t xs[K][kToTile + 1];
+  __shared__ __align__(16) uint64_t cs[K][kToGroup];
+  const int m0 = static_cast<int>(blockIdx.y) * kToGroup;   // first modulus of the group
+  const int mc = min(kToGroup, count - m0);
+  for (int w = threadIdx.x; w < kToGroup * K; w += blockDim.x) {
+    const int m = w / K, j = w % K;
+    cs[j][m] = m < mc ? c[static_cast<size_t>(m0 + m) * K + j] : 0;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t tiles = (n + kToTile - 1) / kToTile;
+  for (size_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const size_t e0 = tile * kToTile;
+    __syncthreads();   // the previous tile's reads are done (and cs is staged)
+    for (int w = threadIdx.x; w < kToTile * K; w += blockDim.x) {
+      const int e = w / K, j = w % K;
+      xs[j][e] = e0 + e < n ? X[e0 * K + w] : 0u;
     }
-    res[static_cast<size_t>(i) * n + e] = Redc64::reduce(acc, mods[i]);
+    __syncthreads();
+    if (4 * warp >= mc) continue;
+    uint32_t acc[2][4][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[h][q][t] = 0;
+#pragma unroll 8
+    for (int j = 0; j < K; ++j) {
+      const uint32_t v0 = xs[j][lane], v1 = xs[j][lane + 32];
+      const ulonglong2 ca = *reinterpret_cast<const ulonglong2*>(&cs[j][4 * warp]);
+      const ulonglong2 cb = *reinterpret_cast<const ulonglong2*>(&cs[j][4 * warp + 2]);
+      mac_limb_word(acc[0][0], v0, ca.x);
+      mac_limb_word(acc[0][1], v0, ca.y);
+      mac_limb_word(acc[0][2], v0, cb.x);
+      mac_limb_word(acc[0][3], v0, cb.y);
+      mac_limb_word(acc[1][0], v1, ca.x);
+      mac_limb_word(acc[1][1], v1, ca.y);
+      mac_limb_word(acc[1][2], v1, cb.x);
+      mac_limb_word(acc[1][3], v1, cb.y);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = m0 + 4 * warp + q;
+      if (i >= count) break;
+      const WordConst64 m = mods[i];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const size_t e = e0 + lane + 32 * h;
+        if (e >= n) continue;
+        const uint32_t* a4 = acc[h][q];
+        const u128 T = (static_cast<u128>((static_cast<uint64_t>(a4[3]) << 32) | a4[2]) << 64) |
+                       ((static_cast<uint64_t>(a4[1]) << 32) | a4[0]);
+        res[static_cast<size_t>(i) * n + e] = Redc64::reduce(T, m);
+      }
+    }
   }
 }
 
@@ -131,10 +189,11 @@ template <int K>
 cudaError_t launch_to(const uint32_t* X, uint64_t* res, size_t n, int count, const WordConst64* mods,
                       const uint64_t* c, cudaStream_t s) {
   const void* k = reinterpret_cast<const void*>(rns_to_kernel<K>);
-  const size_t total = (n + 255) / 256 * static_cast<size_t>(count) * 256;
-  const size_t want = (total + 255) / 256;
-  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256);
-  rns_to_kernel<K><<<static_cast<unsigned>(std::min(want, cap)), 256, 0, s>>>(X, res, n, count, mods, c);
+  const unsigned groups = static_cast<unsigned>((count + kToGroup - 1) / kToGroup);
+  const size_t tiles = (n + kToTile - 1) / kToTile;
+  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256) / groups;
+  const dim3 grid(static_cast<unsigned>(std::max<size_t>(1, std::min(tiles, cap))), groups);
+  rns_to_kernel<K><<<grid, 256, 0, s>>>(X, res, n, count, mods, c);
   return cudaGetLastError();
 }
 
