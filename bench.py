@@ -70,6 +70,9 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the per-config measurements after the main step")
     p.add_argument("--serving-jobs", type=int, default=2000)
+    p.add_argument("--extra", action="append", default=[], metavar="NAME",
+                   help="run only this per-config measurement (repeatable; e.g. rns_convert, "
+                        "sweep_r16, cios) and print {\"extras\": {...}}; for profiling")
     p.add_argument("--log2-pairs", type=int, default=26,
                    help="pairs per modulus = 2^this (26 is the benchmark workload)")
     a = p.parse_args()
@@ -521,21 +524,30 @@ def extra_rns(mg, stream):
     ms_to = _events_ms(f, 20, stream)
     ms_from = _events_ms(g, 20, stream)
     assert torch.equal(X, Y)
-    # 32-bit integer operations per element: to_residues 32 moduli x 64 limbs x
-    # (2 multiply-adds for a 32x64-bit product + 4 adds into the 128-bit sum) +
-    # 32 REDC (~30); from_residues twice that plus 32 x 64 limb updates (~8)
-    ops_to = 32 * 64 * 6 + 32 * 30
-    ops_from = 2 * ops_to + 32 * 64 * 8
+    # 32x32 -> 64-bit limb products (lo + hi) the algorithms need per element.
+    # to_residues: each of the 32 residues sums limbs(X) limb-by-word products
+    # (2 limb products each) and ends in one 64-bit REDC (about 12).
+    # from_residues, step i: the partial value has limbs(Pi_i) limbs; its
+    # residue (2 per limb), the digit (one 64-bit product and two REDCs, about
+    # 28) and the update by v_i Pi_i (2 per limb of Pi_i).
+    lx = -(-_product(ps).bit_length() // 32)
+    lpi = [-(-_product(ps[:i]).bit_length() // 32) if i else 1 for i in range(32)]
+    prods_to = 32 * (2 * lx + 12)
+    prods_from = sum(4 * l + 28 for l in lpi)
     r.close()
+    a_to = n * prods_to / (ms_to * 1e-3)
+    a_from = n * prods_from / (ms_from * 1e-3)
     return {"workload": "2^17 integers below P, 32 primes of 60-62 bits",
             "to_residues_us": round(ms_to * 1e3, 1), "from_residues_us": round(ms_from * 1e3, 1),
             "to_melem_s": round(n / (ms_to * 1e-3) / 1e6, 1),
             "from_melem_s": round(n / (ms_from * 1e-3) / 1e6, 1),
-            "roofline": {"bound": "alu", "unit": "T int-ops/s", "peak": round(ISSUE_PEAK / 1e12, 2),
-                         "achieved_to": round(n * ops_to / (ms_to * 1e-3) / 1e12, 2),
-                         "achieved_from": round(n * ops_from / (ms_from * 1e-3) / 1e12, 2),
-                         "frac_to": round(n * ops_to / (ms_to * 1e-3) / ISSUE_PEAK, 3),
-                         "frac_from": round(n * ops_from / (ms_from * 1e-3) / ISSUE_PEAK, 3)}}
+            "roofline": {"bound": "alu", "unit": "T limb-products/s (32x32->64, lo+hi)",
+                         "peak": round(LIMB_PRODUCT_PEAK / 1e12, 3),
+                         "limb_products_per_element": {"to": prods_to, "from": prods_from},
+                         "achieved_to": round(a_to / 1e12, 3),
+                         "achieved_from": round(a_from / 1e12, 3),
+                         "frac_to": round(a_to / LIMB_PRODUCT_PEAK, 3),
+                         "frac_from": round(a_from / LIMB_PRODUCT_PEAK, 3)}}
 
 
 def _product(xs):
@@ -801,8 +813,32 @@ def run_reference(args):
     }
 
 
+def run_extras_only(names):
+    import torch
+    import paper_2402_00675_gb300 as mg
+    mg.build()
+    peak = 6800.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f).get("hbm_gbs") or peak
+    except OSError:
+        pass
+    stream = torch.cuda.current_stream()
+    table = {"redc32_2p20": extra_redc32, "rns64_batched": extra_rns64, "cios": extra_cios,
+             "limb_variants": extra_limb_variants, "sweep_r16": extra_sweep, "ntt": extra_ntt,
+             "dot_lazy": extra_dot, "rns_convert": extra_rns}
+    out = {}
+    for name in names:
+        fn = table[name]
+        out[name] = fn(mg, stream, peak) if fn.__code__.co_argcount == 3 else fn(mg, stream)
+    return {"extras": out}
+
+
 def main():
     args = parse_args()
+    if args.extra:
+        print(json.dumps(run_extras_only(args.extra)), flush=True)
+        return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res), flush=True)

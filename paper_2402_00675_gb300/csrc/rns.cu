@@ -21,7 +21,9 @@
 // X_{<i} = sum_{j<i} v_j Pi_j is the partial value already built.  One thread
 // per element keeps X in registers as 32-bit limbs; each step reduces X_{<i}
 // modulo p_i with the lazy accumulation above, forms v_i with one REDC
-// (Pi_i^{-1} kept in Montgomery form), and adds v_i Pi_i limb by limb.  The
+// (Pi_i^{-1} kept in Montgomery form), and adds v_i Pi_i limb by limb.  Since
+// X_{<i} < Pi_i, both passes of step i run only over the limbs of Pi_i and
+// Pi_{i+1} (in blocks of four, a warp-uniform skip), about half of all.  The
 // result is the unique X in [0, P), P = prod p_i, with no quotient estimate
 // and no correction step.
 #include <algorithm>
@@ -117,6 +119,15 @@ __global__ void __launch_bounds__(256) rns_to_kernel(const uint32_t* __restrict_
   }
 }
 
+// Dynamic shared memory of the residues -> big kernel: the constants of
+// every step, staged once per block (the steps read them in lock step, so
+// every read is a broadcast).
+size_t from_smem_bytes(int K, int count) {
+  return static_cast<size_t>(count) * K * (sizeof(uint64_t) + sizeof(uint32_t)) +
+         static_cast<size_t>(count) * (sizeof(uint64_t) + sizeof(WordConst64)) +
+         static_cast<size_t>(count + 1) * sizeof(int);
+}
+
 template <int K>
 __global__ void __launch_bounds__(256) rns_from_kernel(const uint64_t* __restrict__ res,
                                                        uint32_t* __restrict__ X, size_t n,
@@ -124,32 +135,73 @@ __global__ void __launch_bounds__(256) rns_from_kernel(const uint64_t* __restric
                                                        const WordConst64* __restrict__ mods,
                                                        const uint64_t* __restrict__ c,
                                                        const uint32_t* __restrict__ pi,
-                                                       const uint64_t* __restrict__ inv) {
+                                                       const uint64_t* __restrict__ inv,
+                                                       const int* __restrict__ live) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* cs = reinterpret_cast<uint64_t*>(smem);                      // count x K
+  WordConst64* ms = reinterpret_cast<WordConst64*>(cs + count * K);      // count
+  uint64_t* is = reinterpret_cast<uint64_t*>(ms + count);                // count
+  uint32_t* ps = reinterpret_cast<uint32_t*>(is + count);                // count x K
+  int* ls = reinterpret_cast<int*>(ps + count * K);                      // count + 1
+  for (int w = threadIdx.x; w < count * K; w += blockDim.x) {
+    cs[w] = c[w];
+    ps[w] = pi[w];
+  }
+  for (int w = threadIdx.x; w < count; w += blockDim.x) {
+    ms[w] = mods[w];
+    is[w] = inv[w];
+  }
+  for (int w = threadIdx.x; w <= count; w += blockDim.x) ls[w] = live[w];
+  __syncthreads();
   for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
        e += static_cast<size_t>(gridDim.x) * blockDim.x) {
     uint32_t x[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) x[j] = 0;
+    uint64_t xi_next = res[e];
     for (int i = 0; i < count; ++i) {
-      const WordConst64 m = mods[i];
-      const uint64_t* ci = c + static_cast<size_t>(i) * K;
-      const uint32_t* pii = pi + static_cast<size_t>(i) * K;
-      // r = X_{<i} mod p_i
-      u128 acc = 0;
+      const uint64_t xi = xi_next;
+      if (i + 1 < count) xi_next = res[static_cast<size_t>(i + 1) * n + e];   // one step ahead
+      const WordConst64 m = ms[i];
+      const uint64_t* ci = cs + i * K;
+      const uint32_t* pii = ps + i * K;
+      // X_{<i} < Pi_i and X_{<i+1} < Pi_{i+1}: only their limbs can be non-zero
+      const int li = ls[i], ln = ls[i + 1];
+      // r = X_{<i} mod p_i, over the live limbs (blocks of 4; the skip is warp-uniform)
+      uint32_t a[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-      for (int j = 0; j < K; ++j) acc += static_cast<u128>(x[j]) * __ldg(ci + j);
-      const uint64_t r = Redc64::reduce(acc, m);
-      const uint64_t xi = res[static_cast<size_t>(i) * n + e];
+      for (int q = 0; q < K / 4; ++q) {
+        if (4 * q < li) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) mac_limb_word(a, x[4 * q + t], ci[4 * q + t]);
+        }
+      }
+      const u128 T = (static_cast<u128>((static_cast<uint64_t>(a[3]) << 32) | a[2]) << 64) |
+                     ((static_cast<uint64_t>(a[1]) << 32) | a[0]);
+      const uint64_t r = Redc64::reduce(T, m);
       const uint64_t d = xi >= r ? xi - r : xi + (m.N - r);
-      // v_i = (x_i - r) Pi_i^{-1} mod p_i   (inv holds Pi_i^{-1} R mod p_i)
-      const uint64_t v = Redc64::reduce(static_cast<u128>(d) * __ldg(inv + i), m);
-      // X += v_i Pi_i; v Pi_j + x_j + carry < 2^95 + 2^64, so the carry fits a word
-      uint64_t carry = 0;
+      // v_i = (x_i - r) Pi_i^{-1} mod p_i   (is holds Pi_i^{-1} R mod p_i)
+      const uint64_t v = Redc64::reduce(static_cast<u128>(d) * is[i], m);
+      const uint32_t v0 = static_cast<uint32_t>(v), v1 = static_cast<uint32_t>(v >> 32);
+      // X += v Pi_i as two rows, v0 Pi_i and v1 Pi_i 2^32, in one pass over the
+      // limbs of Pi_{i+1} (row two lags one limb); each step is a 32x32 product
+      // plus two words, below 2^64, so the carries are single words
+      uint32_t ca = 0, cb = 0, p_prev = 0;
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const u128 t = static_cast<u128>(v) * __ldg(pii + j) + x[j] + carry;
-        x[j] = static_cast<uint32_t>(t);
-        carry = static_cast<uint64_t>(t >> 32);
+      for (int q = 0; q < K / 4; ++q) {
+        if (4 * q < ln) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int j = 4 * q + t;
+            const uint32_t p = pii[j];
+            const uint64_t s0 = static_cast<uint64_t>(v0) * p + x[j] + ca;
+            ca = static_cast<uint32_t>(s0 >> 32);
+            const uint64_t s1 = static_cast<uint64_t>(v1) * p_prev + static_cast<uint32_t>(s0) + cb;
+            cb = static_cast<uint32_t>(s1 >> 32);
+            x[j] = static_cast<uint32_t>(s1);
+            p_prev = p;
+          }
+        }
       }
     }
     uint4* out = reinterpret_cast<uint4*>(X + e * K);
@@ -200,12 +252,21 @@ cudaError_t launch_to(const uint32_t* X, uint64_t* res, size_t n, int count, con
 template <int K>
 cudaError_t launch_from(const uint64_t* res, uint32_t* X, size_t n, int count,
                         const WordConst64* mods, const uint64_t* c, const uint32_t* pi,
-                        const uint64_t* inv, cudaStream_t s) {
+                        const uint64_t* inv, const int* live, cudaStream_t s) {
   const void* k = reinterpret_cast<const void*>(rns_from_kernel<K>);
+  const size_t smem = from_smem_bytes(K, count);
+  if (smem > 48u * 1024u) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
+  if (e != cudaSuccess) return e;
   const size_t want = (n + 255) / 256;
-  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256);
-  rns_from_kernel<K><<<static_cast<unsigned>(std::min(want, cap)), 256, 0, s>>>(
-      res, X, n, count, mods, c, pi, inv);
+  const size_t cap = static_cast<size_t>(device_sm_count()) * static_cast<size_t>(std::max(per_sm, 1));
+  rns_from_kernel<K><<<static_cast<unsigned>(std::min(want, cap)), 256, smem, s>>>(
+      res, X, n, count, mods, c, pi, inv, live);
   return cudaGetLastError();
 }
 
@@ -222,6 +283,7 @@ struct mont_rns {
   uint64_t* d_c = nullptr;
   uint32_t* d_pi = nullptr;
   uint64_t* d_inv = nullptr;
+  int* d_live = nullptr;         // live[i] = limbs of Pi_i, i = 0..count
 };
 
 extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int count) {
@@ -257,6 +319,8 @@ extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int coun
   std::vector<uint64_t> c(static_cast<size_t>(count) * K);
   std::vector<uint32_t> pi(static_cast<size_t>(count) * K, 0u);
   std::vector<uint64_t> inv(count);
+  std::vector<int> live(count + 1);
+  for (int i = 0; i <= count; ++i) live[i] = static_cast<int>(Pi[i].size());
   for (int i = 0; i < count; ++i) {
     const uint64_t p = moduli[i];
     WordConst64 m{};
@@ -287,20 +351,24 @@ extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int coun
   const size_t b_c = c.size() * sizeof(uint64_t);
   const size_t b_pi = pi.size() * sizeof(uint32_t);
   const size_t b_inv = inv.size() * sizeof(uint64_t);
+  const size_t b_live = live.size() * sizeof(int);
   const size_t off_c = (b_mods + 255) / 256 * 256;
   const size_t off_pi = off_c + (b_c + 255) / 256 * 256;
   const size_t off_inv = off_pi + (b_pi + 255) / 256 * 256;
-  cudaError_t e = cudaMalloc(&r->dev, off_inv + b_inv);
+  const size_t off_live = off_inv + (b_inv + 255) / 256 * 256;
+  cudaError_t e = cudaMalloc(&r->dev, off_live + b_live);
   if (e == cudaSuccess) {
     char* base = static_cast<char*>(r->dev);
     r->d_mods = reinterpret_cast<WordConst64*>(base);
     r->d_c = reinterpret_cast<uint64_t*>(base + off_c);
     r->d_pi = reinterpret_cast<uint32_t*>(base + off_pi);
     r->d_inv = reinterpret_cast<uint64_t*>(base + off_inv);
+    r->d_live = reinterpret_cast<int*>(base + off_live);
     e = cudaMemcpy(r->d_mods, mods.data(), b_mods, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(r->d_c, c.data(), b_c, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(r->d_pi, pi.data(), b_pi, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(r->d_inv, inv.data(), b_inv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_live, live.data(), b_live, cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     if (r->dev) cudaFree(r->dev);
@@ -360,10 +428,10 @@ extern "C" int mont_rns_from_residues(mont_rns_t r, const uint64_t* residues, ui
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   switch (r->limbs) {
-    case 8: e = launch_from<8>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
-    case 16: e = launch_from<16>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
-    case 32: e = launch_from<32>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
-    default: e = launch_from<64>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, s); break;
+    case 8: e = launch_from<8>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
+    case 16: e = launch_from<16>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
+    case 32: e = launch_from<32>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
+    default: e = launch_from<64>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
   }
   return cuda_status(e);
 }
