@@ -69,7 +69,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the per-config measurements after the main step")
-    p.add_argument("--serving-jobs", type=int, default=2000)
+    p.add_argument("--serving-jobs", type=int, default=10000)
     p.add_argument("--extra", action="append", default=[], metavar="NAME",
                    help="run only this per-config measurement (repeatable; e.g. rns_convert, "
                         "sweep_r16, cios) and print {\"extras\": {...}}; for profiling")
