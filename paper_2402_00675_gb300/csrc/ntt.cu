@@ -19,6 +19,17 @@
 // y w), and Plantard's prepared b' = (-w R mod N) N^{-1} mod R for the
 // Plantard reduction (so the product -y (-wR) R^{-1} = y w); the data stays
 // in the plain representation [0, N).
+//
+// Lazy butterflies (Plantard twiddles, 4N <= 2^w).  Algorithm 2 returns the
+// exact residue for every 0 <= T <= N 2^w once N <= 2^{w-1} (with m = m1 2^w +
+// m0 its output is floor(k + d), k = (mN - T)/R the residue, d = (N 2^w + m0 N
+// - T)/R in [0, 1) on that domain).  So a twiddle product of any y < 4N is
+// exact, and the coefficients may stay unreduced: forward inputs in [0, 3N),
+// x -> min(x, x - 2N) in [0, 2N), then (x + t, x + N - t) with t = w y in
+// [0, N); inverse inputs in [0, 2N), (X, Y) -> (min(s, s - 2N), w (X + 2N - Y))
+// with s = X + Y.  Unsigned min picks the reduced value because the other one
+// wraps past 2^w.  One min step pair at the end of the forward transform, and
+// the final product by n^{-1} in the inverse, return [0, N).
 #include <cstring>
 #include <new>
 #include <vector>
@@ -69,7 +80,44 @@ __device__ __forceinline__ E sub_n(E x, E t, E N) {
   return x >= t ? x - t : x - t + N;
 }
 
-template <class Op, int LOG2N, int L, bool INV>
+// x - c if x >= c else x, for x < c + 2^w - c: the wrapped difference is larger
+template <class E>
+__device__ __forceinline__ E sub_if_ge(E x, E c) { return min(x, static_cast<E>(x - c)); }
+
+// One butterfly on a register pair: forward (a, b) -> (a + w b, a - w b),
+// inverse (a, b) -> (a + b, (a - b) w); canonical or lazy (see above).
+template <class Op, bool INV, bool LAZY>
+__device__ __forceinline__ void butterfly(typename Op::E& a, typename Op::E& b,
+                                          const typename Tw<Op>::T w, const typename Op::C& c) {
+  using E = typename Op::E;
+  const E N = static_cast<E>(c.N);
+  if constexpr (!INV) {
+    if constexpr (LAZY) {
+      const E x = sub_if_ge<E>(a, 2 * N);
+      const E t = Tw<Op>::mul(b, w, c);
+      a = x + t;
+      b = x + N - t;
+    } else {
+      const E t = Tw<Op>::mul(b, w, c);
+      const E x = a;
+      a = add_n<E>(x, t, N);
+      b = sub_n<E>(x, t, N);
+    }
+  } else {
+    if constexpr (LAZY) {
+      const E s = a + b;
+      const E d = a + 2 * N - b;
+      a = sub_if_ge<E>(s, 2 * N);
+      b = Tw<Op>::mul(d, w, c);
+    } else {
+      const E x = a, y = b;
+      a = add_n<E>(x, y, N);
+      b = Tw<Op>::mul(sub_n<E>(x, y, N), w, c);
+    }
+  }
+}
+
+template <class Op, int LOG2N, int L, bool INV, bool LAZY>
 __device__ __forceinline__ void layer(typename Op::E (&v)[(1 << LOG2N) / 32],
                                       const typename Tw<Op>::T* stw, int lane,
                                       const typename Op::C& c) {
@@ -84,16 +132,7 @@ __device__ __forceinline__ void layer(typename Op::E (&v)[(1 << LOG2N) / 32],
     for (int e = 0; e < EPT; ++e) {
       if ((e & h) == 0) {
         const int k = (n >> (L + 1)) + (e >> (L - 4));
-        const typename Tw<Op>::T w = stw[k];
-        const E x = v[e], y = v[e + h];
-        if constexpr (!INV) {
-          const E t = Tw<Op>::mul(y, w, c);
-          v[e] = add_n<E>(x, t, N);
-          v[e + h] = sub_n<E>(x, t, N);
-        } else {
-          v[e] = add_n<E>(x, y, N);
-          v[e + h] = Tw<Op>::mul(sub_n<E>(x, y, N), w, c);
-        }
+        butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[k], c);
       }
     }
   } else {
@@ -103,35 +142,35 @@ __device__ __forceinline__ void layer(typename Op::E (&v)[(1 << LOG2N) / 32],
       const int k = (n >> (L + 1)) + ((32 * e + lane) >> (L + 1));
       const typename Tw<Op>::T w = stw[k];
       const E other = __shfl_xor_sync(0xFFFFFFFFu, v[e], len);
-      const E x = upper ? other : v[e];
-      const E y = upper ? v[e] : other;
-      if constexpr (!INV) {
-        const E t = Tw<Op>::mul(y, w, c);
-        v[e] = upper ? sub_n<E>(x, t, N) : add_n<E>(x, t, N);
-      } else {
-        v[e] = upper ? Tw<Op>::mul(sub_n<E>(x, y, N), w, c) : add_n<E>(x, y, N);
-      }
+      E x = upper ? other : v[e];
+      E y = upper ? v[e] : other;
+      butterfly<Op, INV, LAZY>(x, y, w, c);   // both lanes, each keeps its half
+      v[e] = upper ? y : x;
     }
   }
 }
 
-template <class Op, int LOG2N, bool INV, int L>
+template <class Op, int LOG2N, bool LAZY, int L>
 __device__ __forceinline__ void layers_fwd(typename Op::E (&v)[(1 << LOG2N) / 32],
                                            const typename Tw<Op>::T* stw, int lane,
                                            const typename Op::C& c) {
-  layer<Op, LOG2N, L, false>(v, stw, lane, c);
-  if constexpr (L > 0) layers_fwd<Op, LOG2N, INV, L - 1>(v, stw, lane, c);
+  layer<Op, LOG2N, L, false, LAZY>(v, stw, lane, c);
+  if constexpr (L > 0) layers_fwd<Op, LOG2N, LAZY, L - 1>(v, stw, lane, c);
 }
 
-template <class Op, int LOG2N, int L>
+template <class Op, int LOG2N, bool LAZY, int L>
 __device__ __forceinline__ void layers_inv(typename Op::E (&v)[(1 << LOG2N) / 32],
                                            const typename Tw<Op>::T* stw, int lane,
                                            const typename Op::C& c) {
-  layer<Op, LOG2N, L, true>(v, stw, lane, c);
-  if constexpr (L + 1 < LOG2N) layers_inv<Op, LOG2N, L + 1>(v, stw, lane, c);
+  layer<Op, LOG2N, L, true, LAZY>(v, stw, lane, c);
+  if constexpr (L + 1 < LOG2N) layers_inv<Op, LOG2N, LAZY, L + 1>(v, stw, lane, c);
 }
 
-template <class Op, int LOG2N, bool INV>
+// [0, 3N) -> [0, N) after a lazy forward transform
+template <class E>
+__device__ __forceinline__ E canon3(E x, E N) { return sub_if_ge<E>(sub_if_ge<E>(x, 2 * N), N); }
+
+template <class Op, int LOG2N, bool INV, bool LAZY>
 __global__ void __launch_bounds__(256) ntt_kernel(const typename Op::E* __restrict__ in,
                                                   typename Op::E* __restrict__ out, size_t batch,
                                                   const typename Tw<Op>::T* __restrict__ tw,
@@ -153,9 +192,13 @@ __global__ void __launch_bounds__(256) ntt_kernel(const typename Op::E* __restri
 #pragma unroll
     for (int e = 0; e < EPT; ++e) v[e] = src[lane + 32 * e];
     if constexpr (!INV) {
-      layers_fwd<Op, LOG2N, INV, LOG2N - 1>(v, stw, lane, c);
+      layers_fwd<Op, LOG2N, LAZY, LOG2N - 1>(v, stw, lane, c);
+      if constexpr (LAZY) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) v[e] = canon3<E>(v[e], static_cast<E>(c.N));
+      }
     } else {
-      layers_inv<Op, LOG2N, 0>(v, stw, lane, c);
+      layers_inv<Op, LOG2N, LAZY, 0>(v, stw, lane, c);
 #pragma unroll
       for (int e = 0; e < EPT; ++e) v[e] = Tw<Op>::mul(v[e], scale, c);
     }
@@ -237,7 +280,7 @@ __device__ __forceinline__ void transpose(E (&v)[1 << (LOG2N - 5)], uint32_t* bu
 
 // All layers of bits [bottom, top) in phase layout lo; descending for the
 // forward transform, ascending for the inverse.
-template <class Op, int LOG2N, bool INV>
+template <class Op, int LOG2N, bool INV, bool LAZY>
 __device__ __forceinline__ void phase_layers(typename Op::E (&v)[1 << (LOG2N - 5)],
                                              const typename Tw<Op>::T* stw, int lane, int lo,
                                              int bottom, int top, const typename Op::C& c) {
@@ -254,22 +297,13 @@ __device__ __forceinline__ void phase_layers(typename Op::E (&v)[1 << (LOG2N - 5
     for (int e = 0; e < EPT; ++e) {
       if ((e & h) == 0) {
         const int i = index_of<LOG2N>(lo, lane, e);
-        const typename Tw<Op>::T w = stw[(n >> (L + 1)) + (i >> (L + 1))];
-        const E x = v[e], y = v[e + h];
-        if constexpr (!INV) {
-          const E t = Tw<Op>::mul(y, w, c);
-          v[e] = add_n<E>(x, t, N);
-          v[e + h] = sub_n<E>(x, t, N);
-        } else {
-          v[e] = add_n<E>(x, y, N);
-          v[e + h] = Tw<Op>::mul(sub_n<E>(x, y, N), w, c);
-        }
+        butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[(n >> (L + 1)) + (i >> (L + 1))], c);
       }
     }
   }
 }
 
-template <class Op, int LOG2N, bool INV>
+template <class Op, int LOG2N, bool INV, bool LAZY>
 __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* __restrict__ in,
                                                          typename Op::E* __restrict__ out,
                                                          size_t batch,
@@ -300,11 +334,11 @@ __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* _
 #pragma unroll
       for (int ph = 0; ph < P::count; ++ph) {
         if (ph > 0) transpose<E, LOG2N>(v, buf, lane, P::lo(ph - 1), P::lo(ph));
-        phase_layers<Op, LOG2N, false>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
+        phase_layers<Op, LOG2N, false, LAZY>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
       }
       E* dst = out + p * n + lane * EPT;                          // last layout: contiguous
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) dst[e] = v[e];
+      for (int e = 0; e < EPT; ++e) dst[e] = LAZY ? canon3<E>(v[e], static_cast<E>(c.N)) : v[e];
     } else {
       const E* src = in + p * n + lane * EPT;
 #pragma unroll
@@ -312,7 +346,7 @@ __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* _
 #pragma unroll
       for (int ph = last; ph >= 0; --ph) {
         if (ph < last) transpose<E, LOG2N>(v, buf, lane, P::lo(ph + 1), P::lo(ph));
-        phase_layers<Op, LOG2N, true>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
+        phase_layers<Op, LOG2N, true, LAZY>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
       }
       E* dst = out + p * n;
 #pragma unroll
@@ -344,7 +378,7 @@ uint32_t bitrev(uint32_t k, int bits) {
   return r;
 }
 
-template <class Op, int LOG2N, bool INV>
+template <class Op, int LOG2N, bool INV, bool LAZY>
 cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, const void* scale,
                        const typename Op::C& c, cudaStream_t s) {
   using T = typename Tw<Op>::T;
@@ -352,13 +386,13 @@ cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, 
   const size_t warps_per_block = 8;
   const size_t want = (batch + warps_per_block - 1) / warps_per_block;
   if constexpr (LOG2N == 5) {   // one coefficient per lane: the shuffle kernel
-    const void* k = reinterpret_cast<const void*>(ntt_kernel<Op, LOG2N, INV>);
+    const void* k = reinterpret_cast<const void*>(ntt_kernel<Op, LOG2N, INV, LAZY>);
     const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(k, 256);
-    ntt_kernel<Op, LOG2N, INV><<<static_cast<unsigned>(want < cap ? want : cap), 256, 0, s>>>(
+    ntt_kernel<Op, LOG2N, INV, LAZY><<<static_cast<unsigned>(want < cap ? want : cap), 256, 0, s>>>(
         static_cast<const E*>(in), static_cast<E*>(out), batch, static_cast<const T*>(tw),
         *static_cast<const T*>(scale), c);
   } else {
-    auto kernel = ntt_phased_kernel<Op, LOG2N, INV>;
+    auto kernel = ntt_phased_kernel<Op, LOG2N, INV, LAZY>;
     const size_t smem = warps_per_block * Planes<E>::count *
                         static_cast<size_t>(Phases<LOG2N>::pad(1 << LOG2N)) * sizeof(uint32_t);
     static bool attr_set = false;   // opt in above 48 KB once per process
@@ -381,17 +415,26 @@ cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, 
   return cudaGetLastError();
 }
 
-template <class Op, bool INV>
+template <class Op, bool INV, bool LAZY = false>
 cudaError_t launch_ntt_n(int log2n, const void* in, void* out, size_t batch, const void* tw,
                          const void* scale, const typename Op::C& c, cudaStream_t s) {
   switch (log2n) {
-    case 5: return launch_ntt<Op, 5, INV>(in, out, batch, tw, scale, c, s);
-    case 6: return launch_ntt<Op, 6, INV>(in, out, batch, tw, scale, c, s);
-    case 7: return launch_ntt<Op, 7, INV>(in, out, batch, tw, scale, c, s);
-    case 8: return launch_ntt<Op, 8, INV>(in, out, batch, tw, scale, c, s);
-    case 9: return launch_ntt<Op, 9, INV>(in, out, batch, tw, scale, c, s);
-    default: return launch_ntt<Op, 10, INV>(in, out, batch, tw, scale, c, s);
+    case 5: return launch_ntt<Op, 5, INV, LAZY>(in, out, batch, tw, scale, c, s);
+    case 6: return launch_ntt<Op, 6, INV, LAZY>(in, out, batch, tw, scale, c, s);
+    case 7: return launch_ntt<Op, 7, INV, LAZY>(in, out, batch, tw, scale, c, s);
+    case 8: return launch_ntt<Op, 8, INV, LAZY>(in, out, batch, tw, scale, c, s);
+    case 9: return launch_ntt<Op, 9, INV, LAZY>(in, out, batch, tw, scale, c, s);
+    default: return launch_ntt<Op, 10, INV, LAZY>(in, out, batch, tw, scale, c, s);
   }
+}
+
+// Plantard plans: lazy butterflies when 4N <= 2^w
+template <class Op, bool INV>
+cudaError_t launch_plantard(bool lazy, int log2n, const void* in, void* out, size_t batch,
+                            const void* tw, const void* scale, const typename Op::C& c,
+                            cudaStream_t s) {
+  return lazy ? launch_ntt_n<Op, INV, true>(log2n, in, out, batch, tw, scale, c, s)
+              : launch_ntt_n<Op, INV, false>(log2n, in, out, batch, tw, scale, c, s);
 }
 
 }  // namespace
@@ -406,6 +449,7 @@ struct mont_ntt {
   void* d_tables = nullptr;   // forward table, inverse table
   size_t tw_bytes = 0;        // bytes of one table entry
   std::vector<unsigned char> scale;  // multiplier form of n^{-1}
+  bool lazy = false;                 // Plantard twiddles with 4N <= 2^w: lazy butterflies
 };
 
 extern "C" int mont_ntt_create(mont_ntt_t* out, mont_ctx_t ctx, int log2n, const uint32_t* psi_limbs) {
@@ -427,6 +471,7 @@ extern "C" int mont_ntt_create(mont_ntt_t* out, mont_ctx_t ctx, int log2n, const
   p->w32 = ctx->w32;
   p->w64 = ctx->w64;
   const bool plantard = ctx->variant == MONT_PLANTARD;
+  p->lazy = plantard && static_cast<u128h>(4) * N <= (u128h{1} << ctx->width);
   const int w = ctx->width;
   p->tw_bytes = (plantard ? 2 : 1) * static_cast<size_t>(w / 8);
   // R mod N for R = 2^w (REDC) or 2^{2w} (Plantard)
@@ -500,15 +545,15 @@ static int ntt_run(mont_ntt_t p, const void* in, void* out, size_t batch, void* 
       e = inv ? launch_ntt_n<Redc32, true>(p->log2n, in, out, batch, tw, sc, p->w32, s)
               : launch_ntt_n<Redc32, false>(p->log2n, in, out, batch, tw, sc, p->w32, s);
     else
-      e = inv ? launch_ntt_n<Plantard32, true>(p->log2n, in, out, batch, tw, sc, p->w32, s)
-              : launch_ntt_n<Plantard32, false>(p->log2n, in, out, batch, tw, sc, p->w32, s);
+      e = inv ? launch_plantard<Plantard32, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s)
+              : launch_plantard<Plantard32, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s);
   } else {
     if (p->variant == MONT_REDC)
       e = inv ? launch_ntt_n<Redc64, true>(p->log2n, in, out, batch, tw, sc, p->w64, s)
               : launch_ntt_n<Redc64, false>(p->log2n, in, out, batch, tw, sc, p->w64, s);
     else
-      e = inv ? launch_ntt_n<Plantard64, true>(p->log2n, in, out, batch, tw, sc, p->w64, s)
-              : launch_ntt_n<Plantard64, false>(p->log2n, in, out, batch, tw, sc, p->w64, s);
+      e = inv ? launch_plantard<Plantard64, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s)
+              : launch_plantard<Plantard64, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s);
   }
   return cuda_status(e);
 }

@@ -196,6 +196,28 @@ def test_plantard_algorithms_exhaustive(n):
                     assert o.sigpredc2_alg(T, N, l, alpha) == o.sigpredc_value(T, N, R)
 
 
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_plantard_exact_on_the_wider_domain(n):
+    """Algorithm 2 returns -T R^{-1} mod N exactly for every 0 <= T <= N 2^n once
+    N <= 2^{n-1} (a wider domain than the paper's T <= N^2, used by the lazy NTT).
+    With m = T N^{-1} mod 2^{2n} = m1 2^n + m0 and k = (mN - T)/2^{2n}, the output is
+    floor(k + d), d = (N 2^n + m0 N - T)/2^{2n}, and 0 <= d < 1 on that domain.
+    Both conditions are needed: outside either, some (N, T) fail."""
+    l = 2 * n
+    R = 1 << l
+    beyond_fails = 0
+    for N in odd_moduli(3, 1 << (n - 1)):
+        want = lambda T: (-T * pow(R, -1, N)) % N
+        for T in range(0, (N << n) + 1):
+            assert o.predc_alg(T, N, l) == want(T), (n, N, T)
+        beyond_fails += sum(o.predc_alg(T, N, l) != want(T)
+                            for T in range((N << n) + 1, (N << n) + (4 << n)))
+    assert beyond_fails > 0                  # the bound on T is not vacuous
+    N = (1 << (n - 1)) + 1                   # just above 2^{n-1}, inside 2^n / phi
+    assert o.plantard_bound_ok(N, n)
+    assert any(o.predc_alg(T, N, l) != (-T * pow(R, -1, N)) % N for T in range(0, (N << n) + 1))
+
+
 def test_plantard_bound_exact_against_decimal():
     decimal.getcontext().prec = 80
     phi = (1 + decimal.Decimal(5).sqrt()) / 2
