@@ -405,17 +405,17 @@ def extra_sweep(mg, stream):
     return out
 
 
-# 32-bit integer operations per butterfly of the algorithm each plan runs.
-# REDC twiddles: the product plus a modular add and a modular subtract, 14 at
-# 32 bits (product, m, high product with N, carry add, conditional
-# subtraction, 3 + 3).  Plantard's prepared twiddles with lazy butterflies
-# (the benchmark's moduli have 4N <= 2^w): the product (two products and one
-# product with N, 3), x reduced below 2N (2), x + t and x + N - t (2), plus the
-# final reduction of every coefficient below N amortised over the butterflies
-# (1), 8.  64-bit words, counting every 64-bit product in 32-bit multiply-adds
-# (4 for a full or high product, 3 for a low one) and 64-bit adds as 2: REDC 37,
-# Plantard lazy 26; see the design doc
-NTT_BUTTERFLY_OPS = {(0, 32): 14, (2, 32): 8, (0, 64): 37, (2, 64): 26}
+# 32-bit integer operations per butterfly of the algorithm each plan runs; the
+# benchmark's moduli have 4N <= 2^w, so both kinds of twiddle run lazy
+# butterflies (coefficients kept below 4N, reduced below N once at the end).
+# REDC twiddles: REDC without its final subtraction (the product, m, the high
+# product with N, the carry and the add, 6), x reduced below 2N (2), x + t and
+# x + 2N - t (2), the final reduction amortised over the butterflies (1): 11.
+# Plantard's prepared twiddles: the product (two products and one product with
+# N, 3), then 2 + 2 + 1 as above: 8.  64-bit words, counting every 64-bit
+# product in 32-bit multiply-adds (4 for a full or high product, 3 for a low
+# one) and 64-bit adds as 2: REDC 30, Plantard 26; see the design doc
+NTT_BUTTERFLY_OPS = {(0, 32): 11, (2, 32): 8, (0, 64): 30, (2, 64): 26}
 
 
 def extra_ntt(mg, stream, peak):

@@ -20,16 +20,18 @@
 // Plantard reduction (so the product -y (-wR) R^{-1} = y w); the data stays
 // in the plain representation [0, N).
 //
-// Lazy butterflies (Plantard twiddles, 4N <= 2^w).  Algorithm 2 returns the
-// exact residue for every 0 <= T <= N 2^w once N <= 2^{w-1} (with m = m1 2^w +
-// m0 its output is floor(k + d), k = (mN - T)/R the residue, d = (N 2^w + m0 N
-// - T)/R in [0, 1) on that domain).  So a twiddle product of any y < 4N is
-// exact, and the coefficients may stay unreduced: forward inputs in [0, 3N),
-// x -> min(x, x - 2N) in [0, 2N), then (x + t, x + N - t) with t = w y in
-// [0, N); inverse inputs in [0, 2N), (X, Y) -> (min(s, s - 2N), w (X + 2N - Y))
-// with s = X + Y.  Unsigned min picks the reduced value because the other one
-// wraps past 2^w.  One min step pair at the end of the forward transform, and
-// the final product by n^{-1} in the inverse, return [0, N).
+// Lazy butterflies (4N <= 2^w).  Algorithm 2 returns the exact residue for
+// every 0 <= T <= N 2^w once N <= 2^{w-1} (with m = m1 2^w + m0 its output is
+// floor(k + d), k = (mN - T)/R the residue, d = (N 2^w + m0 N - T)/R in
+// [0, 1) on that domain), and REDC without its final subtraction returns
+// (T + mN)/R < 2N for every T < RN.  So a twiddle product t of any y < 4N is
+// below B N (B = 1 for Plantard, 2 for REDC), and the coefficients may stay
+// unreduced: forward inputs below (2 + B) N, x -> min(x, x - 2N) below 2N,
+// then (x + t, x + B N - t); inverse inputs below 2N, (X, Y) -> (min(s, s -
+// 2N), w (X + 2N - Y)) with s = X + Y.  Unsigned min picks the reduced value
+// because the other one wraps past 2^w.  One min step pair at the end of the
+// forward transform, and the final (canonical) product by n^{-1} in the
+// inverse, return [0, N).
 #include <cstring>
 #include <new>
 #include <vector>
@@ -44,28 +46,51 @@ struct Tw;
 template <>
 struct Tw<Redc32> {
   using T = uint32_t;
+  static constexpr uint32_t kB = 2;   // mul_lazy < kB N
   static __device__ __forceinline__ uint32_t mul(uint32_t y, T w, const WordConst32& c) {
     return Redc32::reduce(Redc32::mul(y, w), c);
+  }
+  // REDC without its final subtraction: (T + mN)/R < 2N for T < RN.  The low
+  // words of T and mN cancel, so the carry out of their sum is (T mod R != 0).
+  static __device__ __forceinline__ uint32_t mul_lazy(uint32_t y, T w, const WordConst32& c) {
+    const uint64_t t = static_cast<uint64_t>(y) * w;
+    const uint32_t lo = static_cast<uint32_t>(t);
+    const uint32_t m = lo * c.nprime;
+    return static_cast<uint32_t>(t >> 32) + __umulhi(m, c.N) + (lo != 0u ? 1u : 0u);
   }
 };
 template <>
 struct Tw<Plantard32> {
   using T = uint64_t;
+  static constexpr uint32_t kB = 1;   // exact: below N
   static __device__ __forceinline__ uint32_t mul(uint32_t y, T w, const WordConst32& c) {
+    return Plantard32::mul_pre(y, w, c);
+  }
+  static __device__ __forceinline__ uint32_t mul_lazy(uint32_t y, T w, const WordConst32& c) {
     return Plantard32::mul_pre(y, w, c);
   }
 };
 template <>
 struct Tw<Redc64> {
   using T = uint64_t;
+  static constexpr uint64_t kB = 2;
   static __device__ __forceinline__ uint64_t mul(uint64_t y, T w, const WordConst64& c) {
     return Redc64::reduce(Redc64::mul(y, w), c);
+  }
+  static __device__ __forceinline__ uint64_t mul_lazy(uint64_t y, T w, const WordConst64& c) {
+    const uint64_t lo = y * w;
+    const uint64_t m = lo * c.nprime;
+    return __umul64hi(y, w) + __umul64hi(m, c.N) + (lo != 0u ? 1u : 0u);
   }
 };
 template <>
 struct Tw<Plantard64> {
   using T = u128;
+  static constexpr uint64_t kB = 1;
   static __device__ __forceinline__ uint64_t mul(uint64_t y, T w, const WordConst64& c) {
+    return Plantard64::mul_pre(y, w, c);
+  }
+  static __device__ __forceinline__ uint64_t mul_lazy(uint64_t y, T w, const WordConst64& c) {
     return Plantard64::mul_pre(y, w, c);
   }
 };
@@ -94,9 +119,9 @@ __device__ __forceinline__ void butterfly(typename Op::E& a, typename Op::E& b,
   if constexpr (!INV) {
     if constexpr (LAZY) {
       const E x = sub_if_ge<E>(a, 2 * N);
-      const E t = Tw<Op>::mul(b, w, c);
+      const E t = Tw<Op>::mul_lazy(b, w, c);   // below kB N
       a = x + t;
-      b = x + N - t;
+      b = x + Tw<Op>::kB * N - t;
     } else {
       const E t = Tw<Op>::mul(b, w, c);
       const E x = a;
@@ -108,7 +133,7 @@ __device__ __forceinline__ void butterfly(typename Op::E& a, typename Op::E& b,
       const E s = a + b;
       const E d = a + 2 * N - b;
       a = sub_if_ge<E>(s, 2 * N);
-      b = Tw<Op>::mul(d, w, c);
+      b = Tw<Op>::mul_lazy(d, w, c);
     } else {
       const E x = a, y = b;
       a = add_n<E>(x, y, N);
@@ -428,11 +453,11 @@ cudaError_t launch_ntt_n(int log2n, const void* in, void* out, size_t batch, con
   }
 }
 
-// Plantard plans: lazy butterflies when 4N <= 2^w
+// Lazy butterflies when the plan allows them (4N <= 2^w)
 template <class Op, bool INV>
-cudaError_t launch_plantard(bool lazy, int log2n, const void* in, void* out, size_t batch,
-                            const void* tw, const void* scale, const typename Op::C& c,
-                            cudaStream_t s) {
+cudaError_t launch_lazy(bool lazy, int log2n, const void* in, void* out, size_t batch,
+                        const void* tw, const void* scale, const typename Op::C& c,
+                        cudaStream_t s) {
   return lazy ? launch_ntt_n<Op, INV, true>(log2n, in, out, batch, tw, scale, c, s)
               : launch_ntt_n<Op, INV, false>(log2n, in, out, batch, tw, scale, c, s);
 }
@@ -449,7 +474,7 @@ struct mont_ntt {
   void* d_tables = nullptr;   // forward table, inverse table
   size_t tw_bytes = 0;        // bytes of one table entry
   std::vector<unsigned char> scale;  // multiplier form of n^{-1}
-  bool lazy = false;                 // Plantard twiddles with 4N <= 2^w: lazy butterflies
+  bool lazy = false;                 // 4N <= 2^w: lazy butterflies
 };
 
 extern "C" int mont_ntt_create(mont_ntt_t* out, mont_ctx_t ctx, int log2n, const uint32_t* psi_limbs) {
@@ -471,7 +496,7 @@ extern "C" int mont_ntt_create(mont_ntt_t* out, mont_ctx_t ctx, int log2n, const
   p->w32 = ctx->w32;
   p->w64 = ctx->w64;
   const bool plantard = ctx->variant == MONT_PLANTARD;
-  p->lazy = plantard && static_cast<u128h>(4) * N <= (u128h{1} << ctx->width);
+  p->lazy = static_cast<u128h>(4) * N <= (u128h{1} << ctx->width);
   const int w = ctx->width;
   p->tw_bytes = (plantard ? 2 : 1) * static_cast<size_t>(w / 8);
   // R mod N for R = 2^w (REDC) or 2^{2w} (Plantard)
@@ -542,18 +567,18 @@ static int ntt_run(mont_ntt_t p, const void* in, void* out, size_t batch, void* 
   const void* sc = p->scale.data();
   if (p->width == 32) {
     if (p->variant == MONT_REDC)
-      e = inv ? launch_ntt_n<Redc32, true>(p->log2n, in, out, batch, tw, sc, p->w32, s)
-              : launch_ntt_n<Redc32, false>(p->log2n, in, out, batch, tw, sc, p->w32, s);
+      e = inv ? launch_lazy<Redc32, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s)
+              : launch_lazy<Redc32, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s);
     else
-      e = inv ? launch_plantard<Plantard32, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s)
-              : launch_plantard<Plantard32, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s);
+      e = inv ? launch_lazy<Plantard32, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s)
+              : launch_lazy<Plantard32, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w32, s);
   } else {
     if (p->variant == MONT_REDC)
-      e = inv ? launch_ntt_n<Redc64, true>(p->log2n, in, out, batch, tw, sc, p->w64, s)
-              : launch_ntt_n<Redc64, false>(p->log2n, in, out, batch, tw, sc, p->w64, s);
+      e = inv ? launch_lazy<Redc64, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s)
+              : launch_lazy<Redc64, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s);
     else
-      e = inv ? launch_plantard<Plantard64, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s)
-              : launch_plantard<Plantard64, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s);
+      e = inv ? launch_lazy<Plantard64, true>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s)
+              : launch_lazy<Plantard64, false>(p->lazy, p->log2n, in, out, batch, tw, sc, p->w64, s);
   }
   return cuda_status(e);
 }

@@ -65,9 +65,9 @@ def ntt_cases():
     p32_big = sy.ntt_prime(31, 32, 12, seed=21)          # above 2^31: exercises carries
     p_plant = sy.ntt_prime(30, 31, 12, seed=22)          # inside Plantard's 2^32/phi bound
     rns = sy.rns_primes(1, seed=3)[0]
-    p_lazy_top = sy.ntt_prime(29, 30, 12, seed=24)      # 4N <= 2^32: lazy Plantard, largest values
+    p_lazy_top = sy.ntt_prime(29, 30, 12, seed=24)      # 4N <= 2^32: lazy butterflies, largest values
     return [
-        (p_lazy_top, 32, 2, 10), (p_lazy_top, 32, 2, 5),
+        (p_lazy_top, 32, 2, 10), (p_lazy_top, 32, 2, 5), (p_lazy_top, 32, 0, 10),
         (8380417, 32, 0, 8), (8380417, 32, 2, 8), (3329, 32, 0, 7), (3329, 32, 2, 7),
         (7681, 32, 2, 5), (p32_big, 32, 0, 10), (p_plant, 32, 2, 9), (p_plant, 32, 2, 6),
         (rns, 64, 0, 8), (rns, 64, 2, 10), (rns, 64, 2, 5), (rns, 64, 0, 9),
