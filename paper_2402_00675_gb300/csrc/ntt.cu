@@ -287,20 +287,70 @@ struct Planes<uint64_t> {
   }
 };
 
-// Move the lane's coefficients from phase layout `from` to layout `to`.
+// Move the lane's coefficients from phase layout `from` to layout `to`.  In
+// the last layout (lo = 0) a lane's EPT coefficients are consecutive and stay
+// inside one 32-word row of the padded buffer (starting at a multiple of four
+// words), so that side moves as 128-bit accesses.
 template <class E, int LOG2N>
 __device__ __forceinline__ void transpose(E (&v)[1 << (LOG2N - 5)], uint32_t* buf, int lane,
                                           int lo_from, int lo_to) {
   constexpr int EPT = 1 << (LOG2N - 5);
   constexpr int stride = Phases<LOG2N>::pad(1 << LOG2N);
+  constexpr bool kVec = EPT % 4 == 0;
+  const int row = swz(lane * EPT);
+  if (kVec && lo_from == 0) {
 #pragma unroll
-  for (int e = 0; e < EPT; ++e)
-    Planes<E>::put(buf, stride, swz(index_of<LOG2N>(lo_from, lane, e)), v[e]);
-  __syncwarp();
+    for (int q = 0; q < Planes<E>::count; ++q)
 #pragma unroll
-  for (int e = 0; e < EPT; ++e)
-    v[e] = Planes<E>::get(buf, stride, swz(index_of<LOG2N>(lo_to, lane, e)));
+      for (int j = 0; j < EPT / 4; ++j)
+        *reinterpret_cast<uint4*>(buf + q * stride + row + 4 * j) =
+            make_uint4(static_cast<uint32_t>(static_cast<uint64_t>(v[4 * j]) >> (32 * q)),
+                       static_cast<uint32_t>(static_cast<uint64_t>(v[4 * j + 1]) >> (32 * q)),
+                       static_cast<uint32_t>(static_cast<uint64_t>(v[4 * j + 2]) >> (32 * q)),
+                       static_cast<uint32_t>(static_cast<uint64_t>(v[4 * j + 3]) >> (32 * q)));
+  } else {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      Planes<E>::put(buf, stride, swz(index_of<LOG2N>(lo_from, lane, e)), v[e]);
+  }
   __syncwarp();
+  if (kVec && lo_to == 0) {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) v[e] = 0;
+#pragma unroll
+    for (int q = 0; q < Planes<E>::count; ++q)
+#pragma unroll
+      for (int j = 0; j < EPT / 4; ++j) {
+        const uint4 w = *reinterpret_cast<const uint4*>(buf + q * stride + row + 4 * j);
+        v[4 * j] |= static_cast<E>(static_cast<uint64_t>(w.x) << (32 * q));
+        v[4 * j + 1] |= static_cast<E>(static_cast<uint64_t>(w.y) << (32 * q));
+        v[4 * j + 2] |= static_cast<E>(static_cast<uint64_t>(w.z) << (32 * q));
+        v[4 * j + 3] |= static_cast<E>(static_cast<uint64_t>(w.w) << (32 * q));
+      }
+  } else {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      v[e] = Planes<E>::get(buf, stride, swz(index_of<LOG2N>(lo_to, lane, e)));
+  }
+  __syncwarp();
+}
+
+// Shared-memory slot of twiddle i (layer L holds entries [n >> (L+1), n >> L)).
+// The layers of the last phase (lo = 0) are read by lane t at natural index
+// (t << s) | g, s = K - L - 1: stored instead at g * 32 + t, so a warp's reads
+// are consecutive.  The other layers keep the natural order.
+template <int LOG2N>
+__device__ __forceinline__ int twiddle_slot(int i) {
+  using P = Phases<LOG2N>;
+  constexpr int K = LOG2N - 5;
+  constexpr int top_last = P::top(P::count - 1);   // layers [0, top_last) run at lo = 0
+  if (i == 0) return 0;
+  const int lead = 31 - __clz(i);                  // n >> (L + 1) = 2^lead
+  const int L = LOG2N - 1 - lead;
+  if (L >= top_last) return i;
+  const int s = K - L - 1;
+  const int j = i - (1 << lead);
+  return (1 << lead) + ((j & ((1 << s) - 1)) << 5) + (j >> s);
 }
 
 // All layers of bits [bottom, top) in phase layout lo; descending for the
@@ -322,7 +372,9 @@ __device__ __forceinline__ void phase_layers(typename Op::E (&v)[1 << (LOG2N - 5
     for (int e = 0; e < EPT; ++e) {
       if ((e & h) == 0) {
         const int i = index_of<LOG2N>(lo, lane, e);
-        butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[(n >> (L + 1)) + (i >> (L + 1))], c);
+        const int k = lo == 0 ? (n >> (L + 1)) + ((e >> (L + 1)) << 5) + lane   // permuted layers
+                              : (n >> (L + 1)) + (i >> (L + 1));
+        butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[k], c);
       }
     }
   }
@@ -342,8 +394,8 @@ __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* _
   constexpr int EPT = P::EPT;
   constexpr int per_warp = Planes<E>::count * P::pad(n);
   __shared__ T stw[n];
-  extern __shared__ uint32_t dyn_buf[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) stw[i] = tw[i];
+  extern __shared__ __align__(16) uint32_t dyn_buf[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) stw[twiddle_slot<LOG2N>(i)] = tw[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   uint32_t* buf = dyn_buf + (threadIdx.x >> 5) * per_warp;
