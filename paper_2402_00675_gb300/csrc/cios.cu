@@ -301,7 +301,9 @@ int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y,
     return cuda_status(launch_limb_variant(k, mode, ctx->limbv, static_cast<const uint32_t*>(x),
                                            static_cast<const uint32_t*>(y),
                                            static_cast<uint32_t*>(out), n,
-                                           static_cast<cudaStream_t>(stream), v16));
+                                           static_cast<cudaStream_t>(stream), v16,
+                                           tuned_shape(ctx->width, ctx->variant,
+                                                       static_cast<int>(mode))));
   }
   LaunchShape shape = tuned_shape(ctx->width, ctx->variant, static_cast<int>(mode));
   int team = shape.team > 0 ? shape.team : default_team(k);

@@ -80,7 +80,7 @@ cudaError_t launch_word64(int variant, Mode mode, const WordConst64& c, const vo
 // Multi-limb Algorithms 1-4 (limb_variants.cu); k in {4, 8, 12, 16, 32, 64}.
 cudaError_t launch_limb_variant(int k, Mode mode, const LimbVarConst& c, const uint32_t* x,
                                 const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s,
-                                int vec16);
+                                int vec16, const LaunchShape& shape);
 
 // Number of SMs of the current device (cached per device).
 int device_sm_count();

@@ -227,7 +227,7 @@ __device__ __forceinline__ void store_limbs(uint32_t* p, const uint32_t* v, int 
 }
 
 template <int K>
-__global__ void __launch_bounds__(128) limb_variant_kernel(const uint32_t* __restrict__ x,
+__global__ void __launch_bounds__(256) limb_variant_kernel(const uint32_t* __restrict__ x,
                                                            const uint32_t* __restrict__ y,
                                                            uint32_t* __restrict__ out, size_t n,
                                                            int mode, int vec16,
@@ -290,13 +290,19 @@ __global__ void __launch_bounds__(128) limb_variant_kernel(const uint32_t* __res
   }
 }
 
+// Launch shape from the tuning table (threads 128 or 256, resident blocks
+// per SM; 0 = the occupancy limit).  At k >= 32 fewer resident blocks, to keep
+// the local-memory arrays in L1, measured slower at every setting.
 template <int K>
 cudaError_t launch_k(Mode mode, const LimbVarConst& c, const uint32_t* x, const uint32_t* y,
-                     uint32_t* o, size_t n, cudaStream_t s, int vec16) {
+                     uint32_t* o, size_t n, cudaStream_t s, int vec16, const LaunchShape& shape) {
   const void* kern = reinterpret_cast<const void*>(limb_variant_kernel<K>);
-  const size_t want = (n + 127) / 128;
-  const size_t cap = static_cast<size_t>(device_sm_count()) * resident_blocks(kern, 128);
-  limb_variant_kernel<K><<<static_cast<unsigned>(want < cap ? want : cap), 128, 0, s>>>(
+  const int threads = shape.threads == 256 ? 256 : 128;
+  int per_sm = resident_blocks(kern, threads);
+  if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < per_sm) per_sm = shape.blocks_per_sm;
+  const size_t want = (n + threads - 1) / threads;
+  const size_t grid = static_cast<size_t>(device_sm_count()) * (per_sm > 0 ? per_sm : 1);
+  limb_variant_kernel<K><<<static_cast<unsigned>(want < grid ? want : grid), threads, 0, s>>>(
       x, y, o, n, static_cast<int>(mode), vec16, c);
   return cudaGetLastError();
 }
@@ -305,14 +311,14 @@ cudaError_t launch_k(Mode mode, const LimbVarConst& c, const uint32_t* x, const 
 
 cudaError_t launch_limb_variant(int k, Mode mode, const LimbVarConst& c, const uint32_t* x,
                                 const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s,
-                                int vec16) {
+                                int vec16, const LaunchShape& shape) {
   switch (k) {
-    case 4: return launch_k<4>(mode, c, x, y, o, n, s, vec16);
-    case 8: return launch_k<8>(mode, c, x, y, o, n, s, vec16);
-    case 12: return launch_k<12>(mode, c, x, y, o, n, s, vec16);
-    case 16: return launch_k<16>(mode, c, x, y, o, n, s, vec16);
-    case 32: return launch_k<32>(mode, c, x, y, o, n, s, vec16);
-    case 64: return launch_k<64>(mode, c, x, y, o, n, s, vec16);
+    case 4: return launch_k<4>(mode, c, x, y, o, n, s, vec16, shape);
+    case 8: return launch_k<8>(mode, c, x, y, o, n, s, vec16, shape);
+    case 12: return launch_k<12>(mode, c, x, y, o, n, s, vec16, shape);
+    case 16: return launch_k<16>(mode, c, x, y, o, n, s, vec16, shape);
+    case 32: return launch_k<32>(mode, c, x, y, o, n, s, vec16, shape);
+    case 64: return launch_k<64>(mode, c, x, y, o, n, s, vec16, shape);
   }
   return cudaErrorInvalidConfiguration;
 }
