@@ -223,3 +223,27 @@ def test_pipe_runs_multilimb_variants():
     torch.cuda.synchronize()
     assert from_dev(out, k, True) == [o.mul_value(3, x, y, N, l) for x, y in zip(a, b)]
     pipe.close()
+
+
+@pytest.mark.parametrize("k", [8, 32])
+def test_launch_shapes_do_not_change_results(k):
+    """Tuned launch shapes (threads, resident blocks per SM) change speed only."""
+    rnd = random.Random(500 + k)
+    variant = mg.MONT_SIGNED_PLANTARD2
+    l = 64 * k
+    N = moduli(variant, k, 1, rnd)[1]
+    ctx = mg.mont_ctx_create(N, l, variant, alpha=1, n_limbs=k)
+    cnt = 3000 if k == 8 else 700
+    a, b = operands(variant, N, cnt, rnd), operands(variant, N, cnt, rnd)
+    want = [o.mul_value(variant, x, y, N, l, 1) for x, y in zip(a, b)]
+    da, db = to_dev(a, k), to_dev(b, k)
+    try:
+        for shape in ({"threads": 128, "blocks_per_sm": 1}, {"threads": 256, "blocks_per_sm": 0},
+                      {"threads": 256, "blocks_per_sm": 3}, None):
+            mg.mont_tune_set(32 * k, variant, 0, shape)
+            out = torch.zeros(cnt * k, dtype=torch.uint32, device="cuda")
+            mg.mont_mul(ctx, da, db, out, n=cnt)
+            torch.cuda.synchronize()
+            assert from_dev(out, k, True) == want, shape
+    finally:
+        mg.mont_tune_set(32 * k, variant, 0, None)
