@@ -235,35 +235,47 @@ __global__ void __launch_bounds__(256) ntt_kernel(const typename Op::E* __restri
 
 // ------------------------------------------------------------ phased kernel
 //
-// For n >= 64 each lane holds EPT = n/32 coefficients, so K = log2(n) - 5
-// index bits can vary inside a lane.  The transform runs in phases; phase ph
-// puts the index bits [lo, lo + K), lo = max(0, m - (ph + 1) K), inside the
-// lane (element e supplies them) and the other five bits in the lane number:
-//     i(ph, lane, e) = ((lane >> lo) << (lo + K)) | (e << lo) | (lane & (2^lo - 1)),
+// For n >= 64 a group of 2^LB lanes owns one polynomial, each lane holding
+// EPT = 2^K coefficients, K = max(log2 n - 5, 4): a whole warp per polynomial
+// from n = 512, a half-warp at n = 256, 8 lanes at 128, 4 at 64 (fewer
+// phases, hence fewer shared-memory transposes, than one coefficient row per
+// lane).  The transform runs in phases; phase ph puts the index bits [lo,
+// lo + K), lo = max(0, m - (ph + 1) K), inside the lane (element e supplies
+// them) and the other LB bits in the lane's number t within its group:
+//     i(ph, t, e) = ((t >> lo) << (lo + K)) | (e << lo) | (t & (2^lo - 1)),
 // so every butterfly of the phase's layers pairs two registers of one lane.
-// Between phases the warp rewrites its coefficients through shared memory
-// (one plane of 32-bit words per word of the element; address i + 4 (i >> 5)
-// spreads a phase's accesses over the banks).  Phase 0 is i = 32 e + lane
-// (coalesced element loads), the last phase is i = EPT lane + e (each lane
-// owns EPT consecutive coefficients: vector accesses).
+// Between phases the group rewrites its coefficients through its own region
+// of shared memory (one plane of 32-bit words per word of the element;
+// address i + 4 (i >> 5) spreads a phase's accesses over the banks, and the
+// groups of a warp sit 2^LB words apart modulo 32 so that they use different
+// banks).  Phase 0 is i = 2^LB e + t (coalesced element loads), the last
+// phase is i = EPT t + e (each lane owns EPT consecutive coefficients:
+// vector accesses).
 
 template <int LOG2N>
 struct Phases {
   static constexpr int m = LOG2N;
-  static constexpr int K = LOG2N - 5;
+  static constexpr int K = LOG2N - 5 > 4 ? LOG2N - 5 : 4;   // coefficient bits per lane
+  static constexpr int LB = m - K;                           // lane bits of a group
+  static constexpr int GPW = 32 >> LB;                       // polynomials per warp
   static constexpr int EPT = 1 << K;
   static constexpr int count = (m + K - 1) / K;
   __host__ __device__ static constexpr int lo(int ph) { return m - (ph + 1) * K > 0 ? m - (ph + 1) * K : 0; }
   __host__ __device__ static constexpr int top(int ph) { return m - ph * K; }   // bits [bottom, top) butterflied in ph
   __host__ __device__ static constexpr int bottom(int ph) { return lo(ph); }
   __host__ __device__ static constexpr int pad(int n) { return n + (n >> 3); }
+  static constexpr int plane = pad(1 << m);                  // words of one plane
+  // words of one group's region with `planes` planes, 2^LB (mod 32) apart
+  __host__ __device__ static constexpr int group_words(int planes) {
+    return (planes * plane + 31) / 32 * 32 + (LB < 5 ? (1 << LB) : 0);
+  }
 };
 
 __device__ __forceinline__ int swz(int i) { return i + ((i >> 5) << 2); }
 
 template <int LOG2N>
 __device__ __forceinline__ int index_of(int lo, int lane, int e) {
-  constexpr int K = LOG2N - 5;
+  constexpr int K = Phases<LOG2N>::K;
   return ((lane >> lo) << (lo + K)) | (e << lo) | (lane & ((1 << lo) - 1));
 }
 
@@ -287,15 +299,16 @@ struct Planes<uint64_t> {
   }
 };
 
-// Move the lane's coefficients from phase layout `from` to layout `to`.  In
-// the last layout (lo = 0) a lane's EPT coefficients are consecutive and stay
-// inside one 32-word row of the padded buffer (starting at a multiple of four
+// Move the lane's coefficients from phase layout `from` to layout `to` (buf:
+// the group's region, lane: the lane's number in its group).  In the last
+// layout (lo = 0) a lane's EPT coefficients are consecutive and stay inside
+// one 32-word row of the padded buffer (starting at a multiple of four
 // words), so that side moves as 128-bit accesses.
 template <class E, int LOG2N>
-__device__ __forceinline__ void transpose(E (&v)[1 << (LOG2N - 5)], uint32_t* buf, int lane,
+__device__ __forceinline__ void transpose(E (&v)[Phases<LOG2N>::EPT], uint32_t* buf, int lane,
                                           int lo_from, int lo_to) {
-  constexpr int EPT = 1 << (LOG2N - 5);
-  constexpr int stride = Phases<LOG2N>::pad(1 << LOG2N);
+  constexpr int EPT = Phases<LOG2N>::EPT;
+  constexpr int stride = Phases<LOG2N>::plane;
   constexpr bool kVec = EPT % 4 == 0;
   const int row = swz(lane * EPT);
   if (kVec && lo_from == 0) {
@@ -336,13 +349,14 @@ __device__ __forceinline__ void transpose(E (&v)[1 << (LOG2N - 5)], uint32_t* bu
 }
 
 // Shared-memory slot of twiddle i (layer L holds entries [n >> (L+1), n >> L)).
-// The layers of the last phase (lo = 0) are read by lane t at natural index
-// (t << s) | g, s = K - L - 1: stored instead at g * 32 + t, so a warp's reads
-// are consecutive.  The other layers keep the natural order.
+// The layers of the last phase (lo = 0) are read by group lane t at natural
+// index (t << s) | g, s = K - L - 1: stored instead at g 2^LB + t, so a
+// group's reads are consecutive (and the groups of a warp read the same
+// words).  The other layers keep the natural order.
 template <int LOG2N>
 __device__ __forceinline__ int twiddle_slot(int i) {
   using P = Phases<LOG2N>;
-  constexpr int K = LOG2N - 5;
+  constexpr int K = P::K;
   constexpr int top_last = P::top(P::count - 1);   // layers [0, top_last) run at lo = 0
   if (i == 0) return 0;
   const int lead = 31 - __clz(i);                  // n >> (L + 1) = 2^lead
@@ -350,18 +364,19 @@ __device__ __forceinline__ int twiddle_slot(int i) {
   if (L >= top_last) return i;
   const int s = K - L - 1;
   const int j = i - (1 << lead);
-  return (1 << lead) + ((j & ((1 << s) - 1)) << 5) + (j >> s);
+  return (1 << lead) + ((j & ((1 << s) - 1)) << P::LB) + (j >> s);
 }
 
 // All layers of bits [bottom, top) in phase layout lo; descending for the
 // forward transform, ascending for the inverse.
 template <class Op, int LOG2N, bool INV, bool LAZY>
-__device__ __forceinline__ void phase_layers(typename Op::E (&v)[1 << (LOG2N - 5)],
+__device__ __forceinline__ void phase_layers(typename Op::E (&v)[Phases<LOG2N>::EPT],
                                              const typename Tw<Op>::T* stw, int lane, int lo,
                                              int bottom, int top, const typename Op::C& c) {
   using E = typename Op::E;
   constexpr int n = 1 << LOG2N;
-  constexpr int EPT = n / 32;
+  constexpr int EPT = Phases<LOG2N>::EPT;
+  constexpr int LB = Phases<LOG2N>::LB;
   const E N = static_cast<E>(c.N);
 #pragma unroll
   for (int step = 0; step < LOG2N; ++step) {
@@ -372,7 +387,7 @@ __device__ __forceinline__ void phase_layers(typename Op::E (&v)[1 << (LOG2N - 5
     for (int e = 0; e < EPT; ++e) {
       if ((e & h) == 0) {
         const int i = index_of<LOG2N>(lo, lane, e);
-        const int k = lo == 0 ? (n >> (L + 1)) + ((e >> (L + 1)) << 5) + lane   // permuted layers
+        const int k = lo == 0 ? (n >> (L + 1)) + ((e >> (L + 1)) << LB) + lane   // permuted layers
                               : (n >> (L + 1)) + (i >> (L + 1));
         butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[k], c);
       }
@@ -392,52 +407,95 @@ __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* _
   using P = Phases<LOG2N>;
   constexpr int n = 1 << LOG2N;
   constexpr int EPT = P::EPT;
-  constexpr int per_warp = Planes<E>::count * P::pad(n);
+  constexpr int LB = P::LB;
+  constexpr int group_words = P::group_words(Planes<E>::count);
   __shared__ T stw[n];
   extern __shared__ __align__(16) uint32_t dyn_buf[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) stw[twiddle_slot<LOG2N>(i)] = tw[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  uint32_t* buf = dyn_buf + (threadIdx.x >> 5) * per_warp;
+  const int grp = (threadIdx.x & 31) >> LB;        // group (polynomial) within the warp
+  const int lane = threadIdx.x & ((1 << LB) - 1);  // lane within the group
+  uint32_t* buf = dyn_buf + ((threadIdx.x >> 5) * P::GPW + grp) * group_words;
   const size_t warp = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const size_t nwarps = (static_cast<size_t>(gridDim.x) * blockDim.x) >> 5;
+  const size_t step = ((static_cast<size_t>(gridDim.x) * blockDim.x) >> 5) * P::GPW;
   constexpr int last = P::count - 1;
-  // When a lane's coefficients take at most 32 bytes, the warp's next
-  // polynomial loads while this one is transformed (measured: 2-9% faster at
+  // When a lane's coefficients take at most 64 bytes, the group's next
+  // polynomial loads while this one is transformed (measured 0-9% faster at
   // n = 256, 32 bits; at n = 1024, 64 bits the doubled registers cost 25%).
-  // Polynomials are private to one warp, so in-place calls are safe.
-  constexpr bool kPrefetch = EPT * sizeof(E) <= 32;
+  // Every lane of the warp runs every round (the
+  // transposes synchronise the warp); a group without a polynomial in the last
+  // round computes on zeros and stores nothing.  Polynomials are private to
+  // one group, so in-place calls are safe.
+  constexpr bool kPrefetch = EPT * sizeof(E) <= 64;
   E nxt[EPT];
-  auto load = [&](size_t p) {   // first layout: lane + 32 e (forward), lane EPT + e (inverse)
+  // The lane-contiguous side (forward stores, inverse loads: EPT consecutive
+  // elements per lane) moves as 128-bit accesses when the buffers allow it,
+  // so each 32-byte sector is completed by one lane in at most two accesses.
+  constexpr int VPE = 16 / static_cast<int>(sizeof(E));   // elements per 16-byte vector
+  const bool vec = (EPT % VPE == 0) && ((reinterpret_cast<uintptr_t>(in) |
+                                         reinterpret_cast<uintptr_t>(out)) % 16 == 0);
+  auto load = [&](size_t p) {   // first layout: 2^LB e + lane (forward), EPT lane + e (inverse)
     const E* src = in + p * n;
+    if (p >= batch) {
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) nxt[e] = INV ? src[lane * EPT + e] : src[lane + 32 * e];
+      for (int e = 0; e < EPT; ++e) nxt[e] = E{0};
+    } else if (INV && vec) {
+#pragma unroll
+      for (int j = 0; j < EPT / VPE; ++j) {
+        const uint4 w = reinterpret_cast<const uint4*>(src + lane * EPT)[j];
+        const E* we = reinterpret_cast<const E*>(&w);
+#pragma unroll
+        for (int t = 0; t < VPE; ++t) nxt[j * VPE + t] = we[t];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) nxt[e] = INV ? src[lane * EPT + e] : src[(e << LB) + lane];
+    }
   };
-  if (kPrefetch && warp < batch) load(warp);
-  for (size_t p = warp; p < batch; p += nwarps) {
+  const size_t first = warp * P::GPW;
+  if (kPrefetch && first < batch) load(first + grp);
+  for (size_t base = first; base < batch; base += step) {
+    const size_t p = base + grp;
     E v[EPT];
     if (!kPrefetch) load(p);
 #pragma unroll
     for (int e = 0; e < EPT; ++e) v[e] = nxt[e];
-    if (kPrefetch && p + nwarps < batch) load(p + nwarps);
+    if (kPrefetch && base + step < batch) load(p + step);
     if constexpr (!INV) {
 #pragma unroll
       for (int ph = 0; ph < P::count; ++ph) {
         if (ph > 0) transpose<E, LOG2N>(v, buf, lane, P::lo(ph - 1), P::lo(ph));
         phase_layers<Op, LOG2N, false, LAZY>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
       }
-      E* dst = out + p * n + lane * EPT;                          // last layout: contiguous
+      if (p < batch) {
+        E* dst = out + p * n + lane * EPT;                        // last layout: contiguous
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) dst[e] = LAZY ? canon3<E>(v[e], static_cast<E>(c.N)) : v[e];
+        for (int e = 0; e < EPT; ++e) v[e] = LAZY ? canon3<E>(v[e], static_cast<E>(c.N)) : v[e];
+        if (vec) {
+#pragma unroll
+          for (int j = 0; j < EPT / VPE; ++j) {
+            uint4 w;
+            E* we = reinterpret_cast<E*>(&w);
+#pragma unroll
+            for (int t = 0; t < VPE; ++t) we[t] = v[j * VPE + t];
+            reinterpret_cast<uint4*>(dst)[j] = w;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) dst[e] = v[e];
+        }
+      }
     } else {
 #pragma unroll
       for (int ph = last; ph >= 0; --ph) {
         if (ph < last) transpose<E, LOG2N>(v, buf, lane, P::lo(ph + 1), P::lo(ph));
         phase_layers<Op, LOG2N, true, LAZY>(v, stw, lane, P::lo(ph), P::bottom(ph), P::top(ph), c);
       }
-      E* dst = out + p * n;
+      if (p < batch) {
+        E* dst = out + p * n;
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) dst[lane + 32 * e] = Tw<Op>::mul(v[e], scale, c);
+        for (int e = 0; e < EPT; ++e) dst[(e << LB) + lane] = Tw<Op>::mul(v[e], scale, c);
+      }
     }
   }
 }
@@ -480,8 +538,9 @@ cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, 
         *static_cast<const T*>(scale), c);
   } else {
     auto kernel = ntt_phased_kernel<Op, LOG2N, INV, LAZY>;
-    const size_t smem = warps_per_block * Planes<E>::count *
-                        static_cast<size_t>(Phases<LOG2N>::pad(1 << LOG2N)) * sizeof(uint32_t);
+    using P = Phases<LOG2N>;
+    const size_t smem = warps_per_block * P::GPW *
+                        static_cast<size_t>(P::group_words(Planes<E>::count)) * sizeof(uint32_t);
     static bool attr_set = false;   // opt in above 48 KB once per process
     if (!attr_set) {
       cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel),
