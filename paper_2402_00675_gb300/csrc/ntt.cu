@@ -11,14 +11,14 @@
 // + group, for len = n/2 down to 1; the inverse undoes them in reverse order,
 // (X, Y) -> (X + Y, (X - Y) w^{-1}), and scales by n^{-1} at the end.
 //
-// Mapping: one warp owns one polynomial; lane t holds the n/32 coefficients
-// t + 32 e in registers.  Layers with len >= 32 pair registers of one lane;
-// the five layers with len < 32 pair lane t with lane t ^ len through one
-// shuffle, both lanes computing the same product w y.  Twiddles live in
-// shared memory in multiplier form: w R mod N for REDC (so REDC(y * wR) =
-// y w), and Plantard's prepared b' = (-w R mod N) N^{-1} mod R for the
-// Plantard reduction (so the product -y (-wR) R^{-1} = y w); the data stays
-// in the plain representation [0, N).
+// Mapping: for n = 32 a warp owns a polynomial, one coefficient per lane,
+// and every layer pairs lane t with lane t ^ len through one shuffle, both
+// lanes computing the same product w y; for n >= 64 groups of lanes own a
+// polynomial with several coefficients per lane in registers (the phased
+// kernel below).  Twiddles live in shared memory in multiplier form: w R mod
+// N for REDC (so REDC(y * wR) = y w), and Plantard's prepared b' = (-w R mod
+// N) N^{-1} mod R for the Plantard reduction (so the product -y (-wR) R^{-1}
+// = y w); the data stays in the plain representation [0, N).
 //
 // Lazy butterflies (4N <= 2^w).  Algorithm 2 returns the exact residue for
 // every 0 <= T <= N 2^w once N <= 2^{w-1} (with m = m1 2^w + m0 its output is
@@ -142,37 +142,23 @@ __device__ __forceinline__ void butterfly(typename Op::E& a, typename Op::E& b,
   }
 }
 
+// One layer of the n = 32 transform (one coefficient per lane): lane t
+// pairs with lane t ^ len through one shuffle.
 template <class Op, int LOG2N, int L, bool INV, bool LAZY>
 __device__ __forceinline__ void layer(typename Op::E (&v)[(1 << LOG2N) / 32],
                                       const typename Tw<Op>::T* stw, int lane,
                                       const typename Op::C& c) {
+  static_assert(LOG2N == 5, "the shuffle layers serve n = 32 only");
   using E = typename Op::E;
   constexpr int n = 1 << LOG2N;
-  constexpr int EPT = n / 32;
   constexpr int len = 1 << L;
-  const E N = static_cast<E>(c.N);
-  if constexpr (len >= 32) {
-    constexpr int h = len / 32;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      if ((e & h) == 0) {
-        const int k = (n >> (L + 1)) + (e >> (L - 4));
-        butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[k], c);
-      }
-    }
-  } else {
-    const bool upper = (lane & len) != 0;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int k = (n >> (L + 1)) + ((32 * e + lane) >> (L + 1));
-      const typename Tw<Op>::T w = stw[k];
-      const E other = __shfl_xor_sync(0xFFFFFFFFu, v[e], len);
-      E x = upper ? other : v[e];
-      E y = upper ? v[e] : other;
-      butterfly<Op, INV, LAZY>(x, y, w, c);   // both lanes, each keeps its half
-      v[e] = upper ? y : x;
-    }
-  }
+  const bool upper = (lane & len) != 0;
+  const typename Tw<Op>::T w = stw[(n >> (L + 1)) + (lane >> (L + 1))];
+  const E other = __shfl_xor_sync(0xFFFFFFFFu, v[0], len);
+  E x = upper ? other : v[0];
+  E y = upper ? v[0] : other;
+  butterfly<Op, INV, LAZY>(x, y, w, c);   // both lanes, each keeps its half
+  v[0] = upper ? y : x;
 }
 
 template <class Op, int LOG2N, bool LAZY, int L>
