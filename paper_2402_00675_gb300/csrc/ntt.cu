@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(256) ntt_kernel(const typename Op::E* __restri
 // EPT = 2^K coefficients, K = max(log2 n - 5, 4): a whole warp per polynomial
 // from n = 512, a half-warp at n = 256, 8 lanes at 128, 4 at 64 (fewer
 // phases, hence fewer shared-memory transposes, than one coefficient row per
-// lane).  The transform runs in phases; phase ph puts the index bits [lo,
+// lane); with 64-bit words at n = 1024, K = 4 and two warps per polynomial
+// (32 coefficients of 64 bits per lane overflowed the registers and the
+// instruction cache), their transposes separated by block barriers.  The transform runs in phases; phase ph puts the index bits [lo,
 // lo + K), lo = max(0, m - (ph + 1) K), inside the lane (element e supplies
 // them) and the other LB bits in the lane's number t within its group:
 //     i(ph, t, e) = ((t >> lo) << (lo + K)) | (e << lo) | (t & (2^lo - 1)),
@@ -238,12 +240,15 @@ __global__ void __launch_bounds__(256) ntt_kernel(const typename Op::E* __restri
 // phase is i = EPT t + e (each lane owns EPT consecutive coefficients:
 // vector accesses).
 
-template <int LOG2N>
+template <int LOG2N, int W>
 struct Phases {
   static constexpr int m = LOG2N;
-  static constexpr int K = LOG2N - 5 > 4 ? LOG2N - 5 : 4;   // coefficient bits per lane
+  // coefficient bits per lane: at most 16 64-bit words (two warps per polynomial
+  // at n = 1024), else max(log2 n - 5, 4)
+  static constexpr int K = (W == 2 && LOG2N >= 10) ? 4 : (LOG2N - 5 > 4 ? LOG2N - 5 : 4);
   static constexpr int LB = m - K;                           // lane bits of a group
-  static constexpr int GPW = 32 >> LB;                       // polynomials per warp
+  static constexpr bool kBlock = LB > 5;                     // a group spans several warps
+  static constexpr int GPB = 256 >> LB;                      // polynomials per 256-thread block
   static constexpr int EPT = 1 << K;
   static constexpr int count = (m + K - 1) / K;
   __host__ __device__ static constexpr int lo(int ph) { return m - (ph + 1) * K > 0 ? m - (ph + 1) * K : 0; }
@@ -259,9 +264,9 @@ struct Phases {
 
 __device__ __forceinline__ int swz(int i) { return i + ((i >> 5) << 2); }
 
-template <int LOG2N>
+template <int LOG2N, int W>
 __device__ __forceinline__ int index_of(int lo, int lane, int e) {
-  constexpr int K = Phases<LOG2N>::K;
+  constexpr int K = Phases<LOG2N, W>::K;
   return ((lane >> lo) << (lo + K)) | (e << lo) | (lane & ((1 << lo) - 1));
 }
 
@@ -291,10 +296,12 @@ struct Planes<uint64_t> {
 // one 32-word row of the padded buffer (starting at a multiple of four
 // words), so that side moves as 128-bit accesses.
 template <class E, int LOG2N>
-__device__ __forceinline__ void transpose(E (&v)[Phases<LOG2N>::EPT], uint32_t* buf, int lane,
-                                          int lo_from, int lo_to) {
-  constexpr int EPT = Phases<LOG2N>::EPT;
-  constexpr int stride = Phases<LOG2N>::plane;
+__device__ __forceinline__ void transpose(E (&v)[Phases<LOG2N, Planes<E>::count>::EPT],
+                                          uint32_t* buf, int lane, int lo_from, int lo_to) {
+  using P = Phases<LOG2N, Planes<E>::count>;
+  constexpr int W = Planes<E>::count;
+  constexpr int EPT = P::EPT;
+  constexpr int stride = P::plane;
   constexpr bool kVec = EPT % 4 == 0;
   const int row = swz(lane * EPT);
   if (kVec && lo_from == 0) {
@@ -310,9 +317,9 @@ __device__ __forceinline__ void transpose(E (&v)[Phases<LOG2N>::EPT], uint32_t* 
   } else {
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
-      Planes<E>::put(buf, stride, swz(index_of<LOG2N>(lo_from, lane, e)), v[e]);
+      Planes<E>::put(buf, stride, swz(index_of<LOG2N, W>(lo_from, lane, e)), v[e]);
   }
-  __syncwarp();
+  if constexpr (P::kBlock) __syncthreads(); else __syncwarp();
   if (kVec && lo_to == 0) {
 #pragma unroll
     for (int e = 0; e < EPT; ++e) v[e] = 0;
@@ -329,9 +336,9 @@ __device__ __forceinline__ void transpose(E (&v)[Phases<LOG2N>::EPT], uint32_t* 
   } else {
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
-      v[e] = Planes<E>::get(buf, stride, swz(index_of<LOG2N>(lo_to, lane, e)));
+      v[e] = Planes<E>::get(buf, stride, swz(index_of<LOG2N, W>(lo_to, lane, e)));
   }
-  __syncwarp();
+  if constexpr (P::kBlock) __syncthreads(); else __syncwarp();
 }
 
 // Shared-memory slot of twiddle i (layer L holds entries [n >> (L+1), n >> L)).
@@ -339,9 +346,9 @@ __device__ __forceinline__ void transpose(E (&v)[Phases<LOG2N>::EPT], uint32_t* 
 // index (t << s) | g, s = K - L - 1: stored instead at g 2^LB + t, so a
 // group's reads are consecutive (and the groups of a warp read the same
 // words).  The other layers keep the natural order.
-template <int LOG2N>
+template <int LOG2N, int W>
 __device__ __forceinline__ int twiddle_slot(int i) {
-  using P = Phases<LOG2N>;
+  using P = Phases<LOG2N, W>;
   constexpr int K = P::K;
   constexpr int top_last = P::top(P::count - 1);   // layers [0, top_last) run at lo = 0
   if (i == 0) return 0;
@@ -356,13 +363,15 @@ __device__ __forceinline__ int twiddle_slot(int i) {
 // All layers of bits [bottom, top) in phase layout lo; descending for the
 // forward transform, ascending for the inverse.
 template <class Op, int LOG2N, bool INV, bool LAZY>
-__device__ __forceinline__ void phase_layers(typename Op::E (&v)[Phases<LOG2N>::EPT],
-                                             const typename Tw<Op>::T* stw, int lane, int lo,
-                                             int bottom, int top, const typename Op::C& c) {
+__device__ __forceinline__ void phase_layers(
+    typename Op::E (&v)[Phases<LOG2N, Planes<typename Op::E>::count>::EPT],
+    const typename Tw<Op>::T* stw, int lane, int lo, int bottom, int top,
+    const typename Op::C& c) {
   using E = typename Op::E;
+  constexpr int W = Planes<E>::count;
   constexpr int n = 1 << LOG2N;
-  constexpr int EPT = Phases<LOG2N>::EPT;
-  constexpr int LB = Phases<LOG2N>::LB;
+  constexpr int EPT = Phases<LOG2N, W>::EPT;
+  constexpr int LB = Phases<LOG2N, W>::LB;
   const E N = static_cast<E>(c.N);
 #pragma unroll
   for (int step = 0; step < LOG2N; ++step) {
@@ -372,7 +381,7 @@ __device__ __forceinline__ void phase_layers(typename Op::E (&v)[Phases<LOG2N>::
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       if ((e & h) == 0) {
-        const int i = index_of<LOG2N>(lo, lane, e);
+        const int i = index_of<LOG2N, W>(lo, lane, e);
         const int k = lo == 0 ? (n >> (L + 1)) + ((e >> (L + 1)) << LB) + lane   // permuted layers
                               : (n >> (L + 1)) + (i >> (L + 1));
         butterfly<Op, INV, LAZY>(v[e], v[e + h], stw[k], c);
@@ -390,20 +399,24 @@ __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* _
                                                          const typename Op::C c) {
   using E = typename Op::E;
   using T = typename Tw<Op>::T;
-  using P = Phases<LOG2N>;
+  using P = Phases<LOG2N, Planes<E>::count>;
   constexpr int n = 1 << LOG2N;
   constexpr int EPT = P::EPT;
   constexpr int LB = P::LB;
   constexpr int group_words = P::group_words(Planes<E>::count);
   __shared__ T stw[n];
   extern __shared__ __align__(16) uint32_t dyn_buf[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) stw[twiddle_slot<LOG2N>(i)] = tw[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    stw[twiddle_slot<LOG2N, Planes<E>::count>(i)] = tw[i];
   __syncthreads();
-  const int grp = (threadIdx.x & 31) >> LB;        // group (polynomial) within the warp
+  // blockDim.x = 256: the block holds 256 >> LB groups, group g = threads
+  // [g 2^LB, (g + 1) 2^LB); the block walks its polynomials in lock step, so
+  // block barriers between phases are reached by every thread alike
+  const int grp = threadIdx.x >> LB;               // group (polynomial) within the block
   const int lane = threadIdx.x & ((1 << LB) - 1);  // lane within the group
-  uint32_t* buf = dyn_buf + ((threadIdx.x >> 5) * P::GPW + grp) * group_words;
-  const size_t warp = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const size_t step = ((static_cast<size_t>(gridDim.x) * blockDim.x) >> 5) * P::GPW;
+  uint32_t* buf = dyn_buf + grp * group_words;
+  const size_t first = static_cast<size_t>(blockIdx.x) * P::GPB;
+  const size_t step = static_cast<size_t>(gridDim.x) * P::GPB;
   constexpr int last = P::count - 1;
   // When a lane's coefficients take at most 64 bytes, the group's next
   // polynomial loads while this one is transformed (measured 0-9% faster at
@@ -438,7 +451,6 @@ __global__ void __launch_bounds__(256) ntt_phased_kernel(const typename Op::E* _
       for (int e = 0; e < EPT; ++e) nxt[e] = INV ? src[lane * EPT + e] : src[(e << LB) + lane];
     }
   };
-  const size_t first = warp * P::GPW;
   if (kPrefetch && first < batch) load(first + grp);
   for (size_t base = first; base < batch; base += step) {
     const size_t p = base + grp;
@@ -524,8 +536,9 @@ cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, 
         *static_cast<const T*>(scale), c);
   } else {
     auto kernel = ntt_phased_kernel<Op, LOG2N, INV, LAZY>;
-    using P = Phases<LOG2N>;
-    const size_t smem = warps_per_block * P::GPW *
+    using P = Phases<LOG2N, Planes<E>::count>;
+    const size_t want_blocks = (batch + P::GPB - 1) / P::GPB;
+    const size_t smem = static_cast<size_t>(P::GPB) *
                         static_cast<size_t>(P::group_words(Planes<E>::count)) * sizeof(uint32_t);
     static bool attr_set = false;   // opt in above 48 KB once per process
     if (!attr_set) {
@@ -540,7 +553,7 @@ cudaError_t launch_ntt(const void* in, void* out, size_t batch, const void* tw, 
       per_sm = 1;
     }
     const size_t cap = static_cast<size_t>(device_sm_count()) * per_sm;
-    kernel<<<static_cast<unsigned>(want < cap ? want : cap), 256, smem, s>>>(
+    kernel<<<static_cast<unsigned>(want_blocks < cap ? want_blocks : cap), 256, smem, s>>>(
         static_cast<const E*>(in), static_cast<E*>(out), batch, static_cast<const T*>(tw),
         *static_cast<const T*>(scale), c);
   }
