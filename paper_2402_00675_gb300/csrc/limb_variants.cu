@@ -31,9 +31,73 @@ namespace {
 
 constexpr int unroll_for(int k) { return k <= 16 ? 128 : 1; }
 
+// (a0, a1, a2) += x y: a 96-bit column accumulator, in one asm statement so
+// that nothing can clobber the carry flag between the steps.
+__device__ __forceinline__ void mac96(uint32_t (&acc)[3], uint32_t x, uint32_t y) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2])
+      : "r"(x), "r"(y));
+}
+
+// (a0, a1, a2) += (x0, x1) 96-bit.
+__device__ __forceinline__ void add64_96(uint32_t (&acc)[3], uint32_t x0, uint32_t x1) {
+  asm("add.cc.u32 %0, %0, %3;\n\t"
+      "addc.cc.u32 %1, %1, %4;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2])
+      : "r"(x0), "r"(x1));
+}
+
+// out[0, M) = (a[0, KA) * b[0, KB)) mod 2^{32M} by product scanning, for the
+// limb counts whose arrays live in local memory: each output column is
+// summed in a 96-bit register accumulator (a column of up to 64 products
+// stays below 2^71), four columns at a time with a sliding window of b's
+// limbs, so a limb product costs half a local load and a column one store
+// (the row-wise form reads and writes out[i + j] for every product).
+template <int KA, int KB, int M>
+__device__ __noinline__ void mul_scan(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  uint32_t carry0 = 0, carry1 = 0;   // carried into the next column (64 bits)
+  for (int cb = 0; cb < M; cb += 4) {
+    uint32_t s[4][3] = {{carry0, carry1, 0u}, {0u, 0u, 0u}, {0u, 0u, 0u}, {0u, 0u, 0u}};
+    const int ilo = cb - KB + 1 > 0 ? cb - KB + 1 : 0;
+    const int ihi = cb + 3 < KA - 1 ? cb + 3 : KA - 1;
+    // window w[q] = b[cb + q - i] (zero outside [0, KB))
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = cb + q - ilo;
+      w[q] = (j >= 0 && j < KB) ? b[j] : 0u;
+    }
+    for (int i = ilo; i <= ihi; ++i) {
+      const uint32_t ai = a[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mac96(s[q], ai, w[q]);
+      w[3] = w[2];
+      w[2] = w[1];
+      w[1] = w[0];
+      const int j = cb - i - 1;
+      w[0] = (j >= 0 && j < KB) ? b[j] : 0u;
+    }
+    // columns cb..cb+3: emit the low word, carry the rest into the next column
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (cb + q < M) out[cb + q] = s[q][0];
+      if (q < 3) add64_96(s[q + 1], s[q][1], s[q][2]);
+    }
+    carry0 = s[3][1];
+    carry1 = s[3][2];
+  }
+}
+
 // out[0, KA+KB) = a[0, KA) * b[0, KB), unsigned.
 template <int K, int KA, int KB>
 __device__ __forceinline__ void mul_full(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  if constexpr (K > 16) {
+    mul_scan<KA, KB, KA + KB>(a, b, out);
+    return;
+  }
   constexpr int U = unroll_for(K);
 #pragma unroll U
   for (int i = 0; i < KA + KB; ++i) out[i] = 0;
@@ -53,6 +117,10 @@ __device__ __forceinline__ void mul_full(const uint32_t* a, const uint32_t* b, u
 // out[0, M) = (a[0, KA) * b[0, KB)) mod 2^{32M}, unsigned.
 template <int K, int KA, int KB, int M>
 __device__ __forceinline__ void mul_low(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  if constexpr (K > 16) {
+    mul_scan<KA, KB, M>(a, b, out);
+    return;
+  }
   constexpr int U = unroll_for(K);
 #pragma unroll U
   for (int i = 0; i < M; ++i) out[i] = 0;
