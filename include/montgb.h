@@ -636,11 +636,14 @@ int mont_tune_load(const char* path);
 /*
  * mont_probe_int_rate -- measured integer throughput of the current GPU for
  * the instruction mixes of the multi-limb kernels and the sweep: kind 0
- * mad.lo.u32, 1 mad.hi.u32, 2 mad.lo.cc + madc.hi pairs (counted as two),
- * 3 add.u32, 4 mad.wide.u32 (one 32x32->64 multiply-add).  A full-occupancy grid runs `iters` iterations of 8 independent
- * chains per thread; *ops_per_s receives instructions per second (thread
- * instructions).  Synchronous on `stream`.  Measurement support: the paper
- * has no counterpart.
+ * mad.lo.u32, 1 mad.hi.u32, 2 mad.lo.cc + madc.hi pairs (the high product
+ * dependent on the low one; counted as two), 3 add.u32, 4 mad.wide.u32 (one
+ * 32x32->64 multiply-add), 5 a mad.lo.u32 and a mad.hi.u32 on independent
+ * accumulators (counted as two).  A full-occupancy grid runs `iters`
+ * iterations of 8 independent chains per thread; *ops_per_s receives
+ * instructions per second (thread instructions).  MONT_EINVAL for another
+ * kind.  Synchronous on `stream`.  Measurement support: the paper has no
+ * counterpart.
  */
 int mont_probe_int_rate(int kind, int iters, void* stream, double* ops_per_s);
 

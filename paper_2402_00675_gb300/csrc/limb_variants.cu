@@ -91,11 +91,38 @@ __device__ __noinline__ void mul_scan(const uint32_t* a, const uint32_t* b, uint
   }
 }
 
+// The same product scanning fully unrolled, for operands in registers
+// (k <= 16): two accumulators per column (even and odd a-limbs) so that the
+// carry chains of a column can interleave.
+template <int KA, int KB, int M>
+__device__ __forceinline__ void mul_scan_reg(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  uint32_t carry0 = 0, carry1 = 0;
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    uint32_t s0[3] = {carry0, carry1, 0u}, s1[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < KA; ++i) {
+      const int j = c - i;
+      if (j >= 0 && j < KB) {
+        if (i & 1) mac96(s1, a[i], b[j]);
+        else mac96(s0, a[i], b[j]);
+      }
+    }
+    add64_96(s0, s1[0], s1[1]);
+    out[c] = s0[0];
+    carry0 = s0[1];
+    carry1 = s0[2] + s1[2];   // the column total stays below 2^64 + its carry: no overflow
+  }
+}
+
 // out[0, KA+KB) = a[0, KA) * b[0, KB), unsigned.
 template <int K, int KA, int KB>
 __device__ __forceinline__ void mul_full(const uint32_t* a, const uint32_t* b, uint32_t* out) {
   if constexpr (K > 16) {
     mul_scan<KA, KB, KA + KB>(a, b, out);
+    return;
+  } else {
+    mul_scan_reg<KA, KB, KA + KB>(a, b, out);
     return;
   }
   constexpr int U = unroll_for(K);
@@ -119,6 +146,9 @@ template <int K, int KA, int KB, int M>
 __device__ __forceinline__ void mul_low(const uint32_t* a, const uint32_t* b, uint32_t* out) {
   if constexpr (K > 16) {
     mul_scan<KA, KB, M>(a, b, out);
+    return;
+  } else {
+    mul_scan_reg<KA, KB, M>(a, b, out);
     return;
   }
   constexpr int U = unroll_for(K);

@@ -9,6 +9,9 @@
 //   kind 2  mad.lo.cc / madc.hi.cc pairs    (the carry chains of a CIOS row)
 //   kind 3  add.u32                         (plain ALU)
 //   kind 4  mad.wide.u32                    (IMAD.WIDE, a full 32x32->64 product + 64-bit addend)
+//   kind 5  mad.lo.u32 and mad.hi.u32 on independent accumulators (the
+//           low and high halves of different limb products, as product
+//           scanning issues them)
 // Each thread runs 8 independent accumulators for `iters` iterations; the
 // rate is instructions per second over the whole grid, timed with CUDA events
 // on the caller's stream.  Results go to a file-scope device sink so the work
@@ -22,9 +25,12 @@ __device__ uint32_t g_probe_sink;
 
 template <int KIND>
 __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t seed, int iters) {
-  uint32_t x[8];
+  uint32_t x[8], y[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) x[j] = seed + threadIdx.x * 8 + j;
+  for (int j = 0; j < 8; ++j) {
+    x[j] = seed + threadIdx.x * 8 + j;
+    y[j] = x[j] ^ 0x5bd1e995u;
+  }
   const uint32_t m = seed | 1u, c = seed ^ 0x9E3779B9u;
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
@@ -39,6 +45,9 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t seed, int iters)
                      : "+r"(x[j]) : "r"(m), "r"(c));
       } else if constexpr (KIND == 3) {
         asm volatile("add.u32 %0, %0, %1;" : "+r"(x[j]) : "r"(c));
+      } else if constexpr (KIND == 5) {
+        asm volatile("mad.lo.u32 %0, %0, %2, %3;\n\tmad.hi.u32 %1, %1, %2, %3;"
+                     : "+r"(x[j]), "+r"(y[j]) : "r"(m), "r"(c));
       } else {
         // both halves feed the chain, so the full 64-bit product is needed
         asm volatile(
@@ -50,7 +59,7 @@ __global__ void __launch_bounds__(256) int_rate_kernel(uint32_t seed, int iters)
   }
   uint32_t acc = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc ^= x[j];
+  for (int j = 0; j < 8; ++j) acc ^= x[j] ^ y[j];
   if (acc == 0x12345678u) g_probe_sink = acc;  // keeps the loop live
 }
 
@@ -68,7 +77,7 @@ cudaError_t launch_rate(cudaStream_t s, int iters, unsigned* grid) {
 using namespace montgb;
 
 extern "C" int mont_probe_int_rate(int kind, int iters, void* stream, double* ops_per_s) {
-  if (kind < 0 || kind > 4 || iters < 1 || !ops_per_s) return MONT_EINVAL;
+  if (kind < 0 || kind > 5 || iters < 1 || !ops_per_s) return MONT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned grid = 0;
   auto launch = [&]() {
@@ -77,7 +86,8 @@ extern "C" int mont_probe_int_rate(int kind, int iters, void* stream, double* op
       case 1: return launch_rate<1>(s, iters, &grid);
       case 2: return launch_rate<2>(s, iters, &grid);
       case 3: return launch_rate<3>(s, iters, &grid);
-      default: return launch_rate<4>(s, iters, &grid);
+      case 4: return launch_rate<4>(s, iters, &grid);
+      default: return launch_rate<5>(s, iters, &grid);
     }
   };
   cudaError_t e = launch();  // warm-up
@@ -97,7 +107,7 @@ extern "C" int mont_probe_int_rate(int kind, int iters, void* stream, double* op
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_status(e);
-  const double per_thread = 8.0 * iters * (kind == 2 ? 2.0 : 1.0);
+  const double per_thread = 8.0 * iters * (kind == 2 || kind == 5 ? 2.0 : 1.0);
   *ops_per_s = per_thread * grid * 256.0 / (ms * 1e-3);
   return MONT_OK;
 }
