@@ -231,6 +231,32 @@ def _events_ms(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
+def measure_link(h_in, d_in, h_out, d_out, stream):
+    """Host link of this machine, measured on the end-to-end leg's own pinned
+    buffers (256 MiB each): one copy in, one copy out, and both at once, each
+    direction on its own stream (GB/s each way)."""
+    import torch
+    nb = h_in.numel() * h_in.element_size()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(do_in, do_out):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for s_, do, fn in ((s_in, do_in, lambda: d_in.copy_(h_in, non_blocking=True)),
+                           (s_out, do_out, lambda: h_out.copy_(d_out, non_blocking=True))):
+            if do:
+                s_.wait_event(ev)
+                with torch.cuda.stream(s_):
+                    fn()
+                stream.wait_stream(s_)
+    ms_in = _events_ms(lambda: run(True, False), 5, stream)
+    ms_out = _events_ms(lambda: run(False, True), 5, stream)
+    ms_both = _events_ms(lambda: run(True, True), 5, stream)
+    return {"h2d_gbs": round(nb / (ms_in * 1e-3) / 1e9, 1),
+            "d2h_gbs": round(nb / (ms_out * 1e-3) / 1e9, 1),
+            "both_each_gbs": round(nb / (ms_both * 1e-3) / 1e9, 1)}
+
+
 def extra_redc32(mg, stream, peak):
     """REDC, R = 2^32, N = 3329, 2^20 pairs: hot (same buffers, L2-resident)
     and cold (16 rotating buffer sets, 201 MB > L2)."""
@@ -705,6 +731,10 @@ def run_ours(args):
     pipe.close()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = whole_job_rate(modmuls_per_step * e2e_steps, world, e2e_ms)
+    link = measure_link(host_in[MODULI[0]][0], dev_in[MODULI[0]][0],
+                        host_out[keys[0]], outs[keys[0]], stream)
+    # each product moves 4 bytes in and 4 bytes out: the link's two-way rate / 4
+    link["ceiling_gmodmul_s"] = round(link["both_each_gbs"] / 4, 2)
 
     # ---------------- roofline of the dominant kernel (the word kernel)
     peaks = {}
@@ -749,7 +779,7 @@ def run_ours(args):
                        "launches_per_step": len(calls), "parallelism": f"replicas x{world}",
                        "l2": "no flush: every operand array is 256 MiB, larger than the 129 MB L2"},
             "e2e": {"value": round(e2e_value, 3), "unit": METRIC, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps, "link": link,
                     "path": f"mont_pipe_run, one call per step: {e2e_distinct} distinct pinned "
                             f"inputs copied in once, 8 outputs copied out, chunks of "
                             f"{e2e_chunk} elements"},
