@@ -44,7 +44,9 @@ struct SweepParams {
   int range_kind;   // RangeKind of the claimed range
 };
 
-template <int V>
+// NONNEG: every T of the chunk is >= 0 (REDC's own domain), so REDC's sum
+// T + mN is formed in one unsigned word without testing T's sign.
+template <int V, bool NONNEG>
 __device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const SweepParams& p) {
   const uint32_t mask = (1u << p.log2R) - 1u;
   const int32_t N = e.N;
@@ -52,7 +54,7 @@ __device__ __forceinline__ int32_t candidate(int32_t T, const SweepN& e, const S
   if constexpr (V == MONT_REDC) {
     // m <- (T mod R) N' mod R;  t <- (T + mN) / R;  if t >= N: t - N
     const uint32_t m = (static_cast<uint32_t>(T) * e.nprime) & mask;
-    if (T >= 0) {
+    if (NONNEG || T >= 0) {
       // T < 2^31 and m N < 2^16 * 2^15: the sum fits an unsigned word
       const uint32_t t = (static_cast<uint32_t>(T) + m * static_cast<uint32_t>(N)) >> p.log2R;
       return static_cast<int32_t>(t >= static_cast<uint32_t>(N) ? t - static_cast<uint32_t>(N) : t);
@@ -157,6 +159,56 @@ __device__ __noinline__ bool record(int32_t T, int32_t r, uint32_t c, uint32_t N
   return false;
 }
 
+// The checks of one chunk: T0 .. T0 + cnt - 1 against the four reference
+// chains c0..c3 (stepped by s4, the tail by s1); returns the counterexamples.
+template <int V, int RK, bool NONNEG>
+__device__ __forceinline__ uint32_t check_chunk(int64_t T0, uint32_t cnt, const SweepN& e,
+                                                const SweepParams& p, uint32_t c0, uint32_t c1,
+                                                uint32_t c2, uint32_t c3, uint32_t s1, uint32_t s4,
+                                                mont_cex* __restrict__ cex,
+                                                unsigned long long* __restrict__ cex_n,
+                                                unsigned long long cap, bool& full) {
+  constexpr bool kUnsignedTarget = (V == MONT_REDC || V == MONT_PLANTARD);
+  const uint32_t N = static_cast<uint32_t>(e.N);
+  uint32_t local = 0;
+  uint32_t Tu = static_cast<uint32_t>(static_cast<int32_t>(T0));
+  uint32_t i = 0;
+  for (; i + 4 <= cnt; i += 4, Tu += 4) {
+    const int32_t Ta = static_cast<int32_t>(Tu), Tb = static_cast<int32_t>(Tu + 1u);
+    const int32_t Tc = static_cast<int32_t>(Tu + 2u), Td = static_cast<int32_t>(Tu + 3u);
+    const int32_t ra = candidate<V, NONNEG>(Ta, e, p), rb = candidate<V, NONNEG>(Tb, e, p);
+    const int32_t rc = candidate<V, NONNEG>(Tc, e, p), rd = candidate<V, NONNEG>(Td, e, p);
+    const bool ga = fast_good<RK>(ra, c0, e), gb = fast_good<RK>(rb, c1, e);
+    const bool gc = fast_good<RK>(rc, c2, e), gd = fast_good<RK>(rd, c3, e);
+    if (!(ga && gb && gc && gd)) {
+      const bool ba = !ga && exact_bad(ra, c0, e), bb = !gb && exact_bad(rb, c1, e);
+      const bool bc = !gc && exact_bad(rc, c2, e), bd = !gd && exact_bad(rd, c3, e);
+      local += static_cast<uint32_t>(ba) + static_cast<uint32_t>(bb) + static_cast<uint32_t>(bc) +
+               static_cast<uint32_t>(bd);
+      if (!full && (ba || bb || bc || bd)) {
+        if (ba && !full) full = record<kUnsignedTarget>(Ta, ra, c0, N, cex, cex_n, cap);
+        if (bb && !full) full = record<kUnsignedTarget>(Tb, rb, c1, N, cex, cex_n, cap);
+        if (bc && !full) full = record<kUnsignedTarget>(Tc, rc, c2, N, cex, cex_n, cap);
+        if (bd && !full) full = record<kUnsignedTarget>(Td, rd, c3, N, cex, cex_n, cap);
+      }
+    }
+    c0 = step_ref<RK>(c0, s4, N);
+    c1 = step_ref<RK>(c1, s4, N);
+    c2 = step_ref<RK>(c2, s4, N);
+    c3 = step_ref<RK>(c3, s4, N);
+  }
+  for (; i < cnt; ++i, ++Tu) {
+    const int32_t T = static_cast<int32_t>(Tu);
+    const int32_t r = candidate<V, NONNEG>(T, e, p);
+    if (!fast_good<RK>(r, c0, e) && exact_bad(r, c0, e)) {
+      ++local;
+      if (!full) full = record<kUnsignedTarget>(T, r, c0, N, cex, cex_n, cap);
+    }
+    c0 = step_ref<RK>(c0, s1, N);
+  }
+  return local;
+}
+
 template <int V, int RK>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ tab, int n_tab,
                                                     uint64_t n_items, SweepParams p,
@@ -164,7 +216,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
                                                     mont_cex* __restrict__ cex,
                                                     unsigned long long* __restrict__ cex_n,
                                                     unsigned long long cap) {
-  constexpr bool kUnsignedTarget = (V == MONT_REDC || V == MONT_PLANTARD);
   const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   bool full = false;  // the example buffer was seen full: stop touching it
   for (uint64_t item = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; item < n_items;
@@ -193,42 +244,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
       c2 = c2 > h ? c2 - N : c2;
       c3 = c3 > h ? c3 - N : c3;
     }
-    uint32_t local = 0;
-    uint32_t Tu = static_cast<uint32_t>(static_cast<int32_t>(T0));
-    uint32_t i = 0;
-    for (; i + 4 <= cnt; i += 4, Tu += 4) {
-      const int32_t Ta = static_cast<int32_t>(Tu), Tb = static_cast<int32_t>(Tu + 1u);
-      const int32_t Tc = static_cast<int32_t>(Tu + 2u), Td = static_cast<int32_t>(Tu + 3u);
-      const int32_t ra = candidate<V>(Ta, e, p), rb = candidate<V>(Tb, e, p);
-      const int32_t rc = candidate<V>(Tc, e, p), rd = candidate<V>(Td, e, p);
-      const bool ga = fast_good<RK>(ra, c0, e), gb = fast_good<RK>(rb, c1, e);
-      const bool gc = fast_good<RK>(rc, c2, e), gd = fast_good<RK>(rd, c3, e);
-      if (!(ga && gb && gc && gd)) {
-        const bool ba = !ga && exact_bad(ra, c0, e), bb = !gb && exact_bad(rb, c1, e);
-        const bool bc = !gc && exact_bad(rc, c2, e), bd = !gd && exact_bad(rd, c3, e);
-        local += static_cast<uint32_t>(ba) + static_cast<uint32_t>(bb) + static_cast<uint32_t>(bc) +
-                 static_cast<uint32_t>(bd);
-        if (!full && (ba || bb || bc || bd)) {
-          if (ba && !full) full = record<kUnsignedTarget>(Ta, ra, c0, N, cex, cex_n, cap);
-          if (bb && !full) full = record<kUnsignedTarget>(Tb, rb, c1, N, cex, cex_n, cap);
-          if (bc && !full) full = record<kUnsignedTarget>(Tc, rc, c2, N, cex, cex_n, cap);
-          if (bd && !full) full = record<kUnsignedTarget>(Td, rd, c3, N, cex, cex_n, cap);
-        }
-      }
-      c0 = step_ref<RK>(c0, s4, N);
-      c1 = step_ref<RK>(c1, s4, N);
-      c2 = step_ref<RK>(c2, s4, N);
-      c3 = step_ref<RK>(c3, s4, N);
-    }
-    for (; i < cnt; ++i, ++Tu) {
-      const int32_t T = static_cast<int32_t>(Tu);
-      const int32_t r = candidate<V>(T, e, p);
-      if (!fast_good<RK>(r, c0, e) && exact_bad(r, c0, e)) {
-        ++local;
-        if (!full) full = record<kUnsignedTarget>(T, r, c0, N, cex, cex_n, cap);
-      }
-      c0 = step_ref<RK>(c0, s1, N);
-    }
+    const uint32_t local =
+        (V == MONT_REDC && T0 >= 0)
+            ? check_chunk<V, RK, true>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full)
+            : check_chunk<V, RK, false>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full);
     if (local) atomicAdd(counts + lo, static_cast<unsigned long long>(local));
   }
 }
