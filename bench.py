@@ -360,13 +360,17 @@ def extra_cios(mg, stream, peak):
 
 
 def extra_limb_variants(mg, stream, peak):
-    """Algorithms 1-4 at 256 and 1024 bits (n = 32k: R = 2^{32k} for
+    """Algorithms 1-4 at 256, 1024 and 2048 bits (n = 32k: R = 2^{32k} for
     Algorithm 1, 2^{64k} for Algorithms 2-4), random odd N at each variant's
-    largest size class, operands uniform in the variant's output range."""
+    largest size class, operands uniform in the variant's output range.  At
+    1024 and 2048 bits 2^17 and 2^15 drawn pairs are tiled 8 times on the
+    device (the kernel has no data-dependent branch; the operands stay larger
+    than L2): enough elements for about nine waves of the grid."""
     import torch
     out = {}
     names = {1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
-    for bits, count in ((256, 1 << 21), (1024, 1 << 17)):
+    for bits, drawn, tile in ((256, 1 << 21, 1), (1024, 1 << 17, 8), (2048, 1 << 15, 8)):
+        count = drawn * tile
         k = bits // 32
         L = mg.lib()
         sp = stream.cuda_stream
@@ -375,12 +379,12 @@ def extra_limb_variants(mg, stream, peak):
             N = sy.random_odd_modulus(top_bits, seed=4 + variant)
             log2R = 2 * bits if variant >= 2 else bits
             ctx = mg.mont_ctx_create(N, log2R, variant, alpha=1, n_limbs=k)
-            a = sy.uniform_limb_residues(N, k, count, seed=40 + variant)
-            b = sy.uniform_limb_residues(N, k, count, seed=80 + variant)
+            a = sy.uniform_limb_residues(N, k, drawn, seed=40 + variant)
+            b = sy.uniform_limb_residues(N, k, drawn, seed=80 + variant)
             if variant != 2:   # signed variants: centre the residues (x - N for x > N/2)
                 a, b = (sy.centred_limb_residues(N, x) for x in (a, b))
-            da = torch.from_numpy(a.reshape(-1)).cuda()
-            db = torch.from_numpy(b.reshape(-1)).cuda()
+            da = torch.from_numpy(a.reshape(-1)).cuda().repeat(tile)
+            db = torch.from_numpy(b.reshape(-1)).cuda().repeat(tile)
             o = torch.empty_like(da)
             f = lambda: L.mont_mul(ctx.handle, da.data_ptr(), db.data_ptr(), o.data_ptr(), count, sp)
             for _ in range(5):

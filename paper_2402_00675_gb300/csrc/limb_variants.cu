@@ -22,7 +22,7 @@
 //
 // One thread per element, grid-stride.  Up to k = 16 the loops are fully
 // unrolled and the arrays live in registers; at k = 32 and 64 they live in
-// local memory.  The variant and the operation are uniform run-time
+// local memory and the products run over 16 x 16-limb register blocks.  The variant and the operation are uniform run-time
 // branches: one kernel per limb count.
 #include "internal.h"
 
@@ -50,44 +50,92 @@ __device__ __forceinline__ void add64_96(uint32_t (&acc)[3], uint32_t x0, uint32
       : "r"(x0), "r"(x1));
 }
 
-// out[0, M) = (a[0, KA) * b[0, KB)) mod 2^{32M} by product scanning, for the
-// limb counts whose arrays live in local memory: each output column is
-// summed in a 96-bit register accumulator (a column of up to 64 products
-// stays below 2^71), four columns at a time with a sliding window of b's
-// limbs, so a limb product costs half a local load and a column one store
-// (the row-wise form reads and writes out[i + j] for every product).
+// (a0, a1, a2) += x, x one word.
+__device__ __forceinline__ void add32_96(uint32_t (&acc)[3], uint32_t x) {
+  asm("add.cc.u32 %0, %0, %3;\n\t"
+      "addc.cc.u32 %1, %1, 0;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2])
+      : "r"(x));
+}
+
+constexpr int kBlk = 16;   // limbs per register block of the local-memory products
+
+// One 16 x 16-limb block product, accumulated: with
+//   v = o[0, 16) (0 unless has_old) + hi + 2^512 (tc1:tc0) + ra rb,
+// o[0, 16) <- v mod 2^512, hi <- (v >> 512) mod 2^512, (tc1:tc0) <- v >> 1024.
+// Columns are summed in 96-bit accumulators (even and odd limbs of ra apart).
+// LOW_ONLY: only the low 16 columns (a truncated product's top block).
+template <bool LOW_ONLY>
+__device__ __forceinline__ void block_mac(const uint32_t (&ra)[kBlk], const uint32_t (&rb)[kBlk],
+                                          uint32_t* o, bool has_old, uint32_t (&hi)[kBlk],
+                                          uint32_t& tc0, uint32_t& tc1) {
+  uint32_t carry0 = 0, carry1 = 0;
+#pragma unroll
+  for (int col = 0; col < (LOW_ONLY ? kBlk : 2 * kBlk); ++col) {
+    uint32_t s0[3] = {carry0, carry1, 0u}, s1[3] = {0u, 0u, 0u};
+    if (col < kBlk) {
+      s1[0] = hi[col];
+      if (has_old) add32_96(s0, o[col]);
+    } else if (col == kBlk) {
+      s1[0] = tc0;
+      s1[1] = tc1;
+    }
+#pragma unroll
+    for (int i = 0; i < kBlk; ++i) {
+      const int j = col - i;
+      if (j >= 0 && j < kBlk) {
+        if (i & 1) mac96(s1, ra[i], rb[j]);
+        else mac96(s0, ra[i], rb[j]);
+      }
+    }
+    add64_96(s0, s1[0], s1[1]);
+    if (col < kBlk) o[col] = s0[0];
+    else hi[col - kBlk] = s0[0];
+    carry0 = s0[1];
+    carry1 = s0[2] + s1[2];   // a column total stays below 2^69: no overflow
+  }
+  if (!LOW_ONLY) {
+    tc0 = carry0;
+    tc1 = carry1;
+  }
+}
+
+// out[0, M) = (a[0, KA) * b[0, KB)) mod 2^{32M} for the limb counts whose
+// arrays live in local memory (k >= 32): schoolbook over 16 x 16-limb
+// blocks, each block product formed by product scanning in registers.  Row I
+// of blocks (a's block I against every block of b) carries the high half of
+// each block product into the next block in registers, so a block costs 16
+// operand loads and 16 loads and stores of the result for 256 limb products.
+// Row I accumulates into blocks I .. I+NB-1, which row I-1 has written, and
+// writes block I+NB first; the row's running sum is below 2^{512(I+1+NB)},
+// so nothing carries past that block.
 template <int KA, int KB, int M>
-__device__ __noinline__ void mul_scan(const uint32_t* a, const uint32_t* b, uint32_t* out) {
-  uint32_t carry0 = 0, carry1 = 0;   // carried into the next column (64 bits)
-  for (int cb = 0; cb < M; cb += 4) {
-    uint32_t s[4][3] = {{carry0, carry1, 0u}, {0u, 0u, 0u}, {0u, 0u, 0u}, {0u, 0u, 0u}};
-    const int ilo = cb - KB + 1 > 0 ? cb - KB + 1 : 0;
-    const int ihi = cb + 3 < KA - 1 ? cb + 3 : KA - 1;
-    // window w[q] = b[cb + q - i] (zero outside [0, KB))
-    uint32_t w[4];
+__device__ __noinline__ void mul_blocked(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  static_assert(KA % kBlk == 0 && KB % kBlk == 0 && M % kBlk == 0 && M <= KA + KB,
+                "block shapes");
+  constexpr int NA = KA / kBlk, NB = KB / kBlk, NM = M / kBlk;
+  for (int I = 0; I < NA && I < NM; ++I) {
+    uint32_t ra[kBlk], hi[kBlk];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = cb + q - ilo;
-      w[q] = (j >= 0 && j < KB) ? b[j] : 0u;
+    for (int t = 0; t < kBlk; ++t) {
+      ra[t] = a[kBlk * I + t];
+      hi[t] = 0u;
     }
-    for (int i = ilo; i <= ihi; ++i) {
-      const uint32_t ai = a[i];
+    uint32_t tc0 = 0, tc1 = 0;
+    const bool has_old = I > 0;
+    for (int J = 0; J < NB && I + J < NM; ++J) {
+      uint32_t rb[kBlk];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) mac96(s[q], ai, w[q]);
-      w[3] = w[2];
-      w[2] = w[1];
-      w[1] = w[0];
-      const int j = cb - i - 1;
-      w[0] = (j >= 0 && j < KB) ? b[j] : 0u;
+      for (int t = 0; t < kBlk; ++t) rb[t] = b[kBlk * J + t];
+      uint32_t* o = out + kBlk * (I + J);
+      if (I + J == NM - 1) block_mac<true>(ra, rb, o, has_old, hi, tc0, tc1);
+      else block_mac<false>(ra, rb, o, has_old, hi, tc0, tc1);
     }
-    // columns cb..cb+3: emit the low word, carry the rest into the next column
+    if (I + NB < NM) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (cb + q < M) out[cb + q] = s[q][0];
-      if (q < 3) add64_96(s[q + 1], s[q][1], s[q][2]);
+      for (int t = 0; t < kBlk; ++t) out[kBlk * (I + NB) + t] = hi[t];
     }
-    carry0 = s[3][1];
-    carry1 = s[3][2];
   }
 }
 
@@ -119,25 +167,9 @@ __device__ __forceinline__ void mul_scan_reg(const uint32_t* a, const uint32_t* 
 template <int K, int KA, int KB>
 __device__ __forceinline__ void mul_full(const uint32_t* a, const uint32_t* b, uint32_t* out) {
   if constexpr (K > 16) {
-    mul_scan<KA, KB, KA + KB>(a, b, out);
-    return;
+    mul_blocked<KA, KB, KA + KB>(a, b, out);
   } else {
     mul_scan_reg<KA, KB, KA + KB>(a, b, out);
-    return;
-  }
-  constexpr int U = unroll_for(K);
-#pragma unroll U
-  for (int i = 0; i < KA + KB; ++i) out[i] = 0;
-#pragma unroll U
-  for (int i = 0; i < KA; ++i) {
-    uint32_t carry = 0;
-#pragma unroll U
-    for (int j = 0; j < KB; ++j) {
-      const uint64_t t = static_cast<uint64_t>(a[i]) * b[j] + out[i + j] + carry;
-      out[i + j] = static_cast<uint32_t>(t);
-      carry = static_cast<uint32_t>(t >> 32);
-    }
-    out[i + KB] = carry;
   }
 }
 
@@ -145,27 +177,9 @@ __device__ __forceinline__ void mul_full(const uint32_t* a, const uint32_t* b, u
 template <int K, int KA, int KB, int M>
 __device__ __forceinline__ void mul_low(const uint32_t* a, const uint32_t* b, uint32_t* out) {
   if constexpr (K > 16) {
-    mul_scan<KA, KB, M>(a, b, out);
-    return;
+    mul_blocked<KA, KB, M>(a, b, out);
   } else {
     mul_scan_reg<KA, KB, M>(a, b, out);
-    return;
-  }
-  constexpr int U = unroll_for(K);
-#pragma unroll U
-  for (int i = 0; i < M; ++i) out[i] = 0;
-#pragma unroll U
-  for (int i = 0; i < KA; ++i) {
-    if (i >= M) break;
-    uint32_t carry = 0;
-#pragma unroll U
-    for (int j = 0; j < KB; ++j) {
-      if (i + j >= M) break;
-      const uint64_t t = static_cast<uint64_t>(a[i]) * b[j] + out[i + j] + carry;
-      out[i + j] = static_cast<uint32_t>(t);
-      carry = static_cast<uint32_t>(t >> 32);
-    }
-    if (i + KB < M) out[i + KB] = carry;
   }
 }
 
@@ -192,6 +206,20 @@ __device__ __forceinline__ void add_masked(uint32_t* x, const uint32_t* y, uint3
     const uint64_t s = static_cast<uint64_t>(x[i]) + (y[i] & mask) + carry;
     x[i] = static_cast<uint32_t>(s);
     carry = static_cast<uint32_t>(s >> 32);
+  }
+}
+
+// x[0, L) -= (y[0, L) & my) + (z[0, L) & mz), modulo 2^{32L}.
+template <int K, int L>
+__device__ __forceinline__ void sub2_masked(uint32_t* x, const uint32_t* y, uint32_t my,
+                                            const uint32_t* z, uint32_t mz) {
+  constexpr int U = unroll_for(K);
+  uint32_t borrow = 0;   // 0, 1 or 2
+#pragma unroll U
+  for (int i = 0; i < L; ++i) {
+    const int64_t d = static_cast<int64_t>(x[i]) - (y[i] & my) - (z[i] & mz) - borrow;
+    x[i] = static_cast<uint32_t>(d);
+    borrow = static_cast<uint32_t>(-(d >> 32));   // d >= -2^33: d >> 32 in {-2, -1, 0}
   }
 }
 
@@ -239,10 +267,24 @@ __device__ __forceinline__ void shifted_product(const uint32_t* q, const LimbVar
                                                 bool round_half, uint32_t* r) {
   constexpr int U = unroll_for(K);
   uint32_t P[2 * K + 1];
-  mul_full<K, K + 1, K>(q, c.N, P);
+  if constexpr (K > 16) {
+    // the blocked product takes whole blocks: q's low K limbs times N, then
+    // the row q_K N 2^{32K} (q_K is 0, 1 or 2^32 - 1)
+    mul_full<K, K, K>(q, c.N, P);
+    uint32_t carry = 0;
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+      const uint64_t t = static_cast<uint64_t>(q[K]) * c.N[j] + P[K + j] + carry;
+      P[K + j] = static_cast<uint32_t>(t);
+      carry = static_cast<uint32_t>(t >> 32);
+    }
+    P[2 * K] = carry;
+  } else {
+    mul_full<K, K + 1, K>(q, c.N, P);
+  }
   // q < 0 stands for q + 2^{32(K+1)}: remove N 2^{32(K+1)} from limbs K+1..2K
   sub_masked<K, K>(P + K + 1, c.N, sign_mask(q[K]));
-  if (round_half) add_pow2<K, 2 * K + 1>(P, 32 * K - 1);
+  if (round_half) add_pow2<K, K + 2>(P + K - 1, 31);   // + 2^{32K-1}: limbs K-1 .. 2K
 #pragma unroll U
   for (int i = 0; i < K; ++i) r[i] = P[K + i];
 }
@@ -356,10 +398,8 @@ __global__ void __launch_bounds__(256) limb_variant_kernel(const uint32_t* __res
           for (int i = 0; i < K; ++i) b[i] = c.dom[i];
         }
         mul_full<K, K, K>(a, b, T);
-        if (is_signed) {                        // T mod 2^{64K} of the signed product
-          sub_masked<K, K>(T + K, b, sign_mask(a[K - 1]));
-          sub_masked<K, K>(T + K, a, sign_mask(b[K - 1]));
-        }
+        if (is_signed)                          // T mod 2^{64K} of the signed product
+          sub2_masked<K, K>(T + K, b, sign_mask(a[K - 1]), a, sign_mask(b[K - 1]));
       }
     }
     uint32_t r[K];
