@@ -714,6 +714,17 @@ def run_ours(args):
     def e2e_step():
         pipe.run(e2e_ops, stream)
 
+    def link_now():
+        lk = measure_link(host_in[MODULI[0]][0], dev_in[MODULI[0]][0],
+                          host_out[keys[0]], outs[keys[0]], stream)
+        # each product moves 4 bytes in and 4 bytes out: the link's two-way rate / 4
+        lk["ceiling_gmodmul_s"] = round(lk["both_each_gbs"] / 4, 2)
+        return lk
+
+    # the host link is shared with other jobs on this host: measured right
+    # before and right after the leg
+    link_before = link_now()
+    host_out[keys[0]].zero_()   # the leg's own copies must write it again
     e2e_step()
     torch.cuda.synchronize()
     if world > 1:
@@ -735,10 +746,7 @@ def run_ours(args):
     pipe.close()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = whole_job_rate(modmuls_per_step * e2e_steps, world, e2e_ms)
-    link = measure_link(host_in[MODULI[0]][0], dev_in[MODULI[0]][0],
-                        host_out[keys[0]], outs[keys[0]], stream)
-    # each product moves 4 bytes in and 4 bytes out: the link's two-way rate / 4
-    link["ceiling_gmodmul_s"] = round(link["both_each_gbs"] / 4, 2)
+    link = {"before": link_before, "after": link_now()}
 
     # ---------------- roofline of the dominant kernel (the word kernel)
     peaks = {}
