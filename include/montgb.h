@@ -599,7 +599,8 @@ typedef struct mont_launch_shape {
   int vec_bytes;      /* word kernels: 32, 16 or 0 (scalar loads)                         */
   int blocks_per_sm;  /* resident blocks per SM the grid is sized for; 0 = occupancy max   */
   int tile_iters;     /* reserved; keep 0                                                   */
-  int team;           /* multi-limb: lanes per element (1, 2, 4, 8, 16); 0 = default       */
+  int team;           /* multi-limb REDC: lanes per element (1, 2, 4, 8, 16); 0 = default;
+                         the other multi-limb variants run one thread per element      */
 } mont_launch_shape;
 
 #define MONT_TUNE_MODE_MUL          0  /* mont_mul (also used by the other modes when tuned) */
