@@ -240,33 +240,39 @@ __device__ __forceinline__ void add_pow2(uint32_t* x, int bit) {
 
 __device__ __forceinline__ uint32_t sign_mask(uint32_t top) { return 0u - (top >> 31); }
 
-// Algorithm 1 at R = 2^{32K}: T (2K limbs, two's complement) -> r (K limbs).
+// The steps of one element use two buffers of local state, reused in turn:
+//   X (2K+1 limbs): T, then the product whose high half is r
+//   Y (3K+1 limbs): the operands a | b, then m (and Algorithm 1's m N)
+// so an element holds 5K+2 limbs whatever the algorithm.  No product below
+// writes a buffer it reads.
+
+// Algorithm 1 at R = 2^{32K}: T in X (2K limbs, two's complement) -> r in
+// X[K, 2K).
 template <int K>
-__device__ __forceinline__ void sig_redc(const uint32_t* T, const LimbVarConst& c, uint32_t* r) {
-  constexpr int U = unroll_for(K);
-  uint32_t m[K];
-  mul_low<K, K, K, K>(T, c.ninv, m);            // m = (T mod R) N^{-1} mod R; signed view = mods R
-  uint32_t P[2 * K];
+__device__ __forceinline__ void sig_redc(uint32_t* X, uint32_t* Y, const LimbVarConst& c) {
+  uint32_t* m = Y;                              // K limbs
+  uint32_t* P = Y + K;                          // 2K limbs
+  mul_low<K, K, K, K>(X, c.ninv, m);            // m = (T mod R) N^{-1} mod R; signed view = mods R
   mul_full<K, K, K>(m, c.N, P);                 // (m mod R) N
-#pragma unroll U
-  for (int i = 0; i < K; ++i) r[i] = T[K + i];  // T >> n (the high limbs, signed)
-  sub_masked<K, K>(r, P + K, 0xFFFFFFFFu);      // - ((m mod R) N >> n)
-  add_masked<K, K>(r, c.N, sign_mask(m[K - 1]));  // m < 0: (m N) >> n = ((m mod R) N >> n) - N
+  const uint32_t m_neg = sign_mask(m[K - 1]);
+  sub_masked<K, K>(X + K, P + K, 0xFFFFFFFFu);  // (T >> n) - ((m mod R) N >> n)
+  add_masked<K, K>(X + K, c.N, m_neg);          // m < 0: (m N) >> n = ((m mod R) N >> n) - N
 }
 
-// m = T N^{-1} mod 2^{64K} (low 2K limbs) for the Plantard family.
+// m = T N^{-1} mod 2^{64K} (low 2K limbs) for the Plantard family: T in X,
+// m in Y[0, 2K).
 template <int K>
-__device__ __forceinline__ void plantard_m(const uint32_t* T, const LimbVarConst& c, uint32_t* m) {
-  mul_low<K, 2 * K, 2 * K, 2 * K>(T, c.ninv, m);
+__device__ __forceinline__ void plantard_m(const uint32_t* X, const LimbVarConst& c, uint32_t* Y) {
+  mul_low<K, 2 * K, 2 * K, 2 * K>(X, c.ninv, Y);
 }
 
-// r = (q N) >> n with q signed of K+1 limbs, plus 2^{n-1} before the shift
-// when round_half is set.  The product is formed on 2K+1 limbs.
+// r = (q N) >> n with q signed of K+1 limbs (Y[K, 2K]), plus 2^{n-1} before
+// the shift when round_half is set.  The product is formed in X (2K+1 limbs;
+// T is no longer needed) and r is X[K, 2K).
 template <int K>
 __device__ __forceinline__ void shifted_product(const uint32_t* q, const LimbVarConst& c,
-                                                bool round_half, uint32_t* r) {
-  constexpr int U = unroll_for(K);
-  uint32_t P[2 * K + 1];
+                                                bool round_half, uint32_t* X) {
+  uint32_t* P = X;
   if constexpr (K > 16) {
     // the blocked product takes whole blocks: q's low K limbs times N, then
     // the row q_K N 2^{32K} (q_K is 0, 1 or 2^32 - 1)
@@ -285,53 +291,48 @@ __device__ __forceinline__ void shifted_product(const uint32_t* q, const LimbVar
   // q < 0 stands for q + 2^{32(K+1)}: remove N 2^{32(K+1)} from limbs K+1..2K
   sub_masked<K, K>(P + K + 1, c.N, sign_mask(q[K]));
   if (round_half) add_pow2<K, K + 2>(P + K - 1, 31);   // + 2^{32K-1}: limbs K-1 .. 2K
-#pragma unroll U
-  for (int i = 0; i < K; ++i) r[i] = P[K + i];
 }
 
-// Algorithm 2 at R = 2^{64K}.
+// Algorithm 2 at R = 2^{64K}: T in X -> r in X[K, 2K).
 template <int K>
-__device__ __forceinline__ void p_redc(const uint32_t* T, const LimbVarConst& c, uint32_t* r) {
+__device__ __forceinline__ void p_redc(uint32_t* X, uint32_t* Y, const LimbVarConst& c) {
   constexpr int U = unroll_for(K);
-  uint32_t m[2 * K];
-  plantard_m<K>(T, c, m);
-  uint32_t q[K + 1];                            // (m >> n) + 1, unsigned
+  plantard_m<K>(X, c, Y);
+  uint32_t* q = Y + K;                          // (m >> n) + 1, unsigned, in place over m's high half
   uint32_t carry = 1;
 #pragma unroll U
   for (int i = 0; i < K; ++i) {
-    const uint32_t s = m[K + i] + carry;
+    const uint32_t s = q[i] + carry;
     carry = s < carry ? 1u : 0u;
     q[i] = s;
   }
   q[K] = carry;
-  shifted_product<K>(q, c, false, r);           // q >= 0: no sign correction applies
+  shifted_product<K>(q, c, false, X);           // q >= 0: no sign correction applies
 }
 
-// Algorithms 3 and 4 at R = 2^{64K}.
+// Algorithms 3 and 4 at R = 2^{64K}: T in X -> r in X[K, 2K).
 template <int K>
-__device__ __forceinline__ void sig_p_redc(const uint32_t* T, const LimbVarConst& c, uint32_t* r) {
+__device__ __forceinline__ void sig_p_redc(uint32_t* X, uint32_t* Y, const LimbVarConst& c) {
   constexpr int U = unroll_for(K);
-  uint32_t m[2 * K];
-  plantard_m<K>(T, c, m);                       // two's complement view = (int_{2n})(T N^{-1})
-  uint32_t q[K + 1];
+  plantard_m<K>(X, c, Y);                       // two's complement view = (int_{2n})(T N^{-1})
+  uint32_t* q = Y + K;                          // in place over m's high half, one limb above
+  const uint32_t m_sign = sign_mask(Y[2 * K - 1]);
   if (c.variant == MONT_SIGNED_PLANTARD) {
     // q = (m + 2^{n-1}) >> n on 2K+1 limbs: add 2^31 to limb K-1, carry upward
-    uint32_t carry = (m[K - 1] + 0x80000000u) < m[K - 1] ? 1u : 0u;
+    uint32_t carry = (Y[K - 1] + 0x80000000u) < Y[K - 1] ? 1u : 0u;
 #pragma unroll U
     for (int i = 0; i < K; ++i) {
-      const uint32_t s = m[K + i] + carry;
+      const uint32_t s = q[i] + carry;
       carry = s < carry ? 1u : 0u;
       q[i] = s;
     }
-    q[K] = sign_mask(m[2 * K - 1]) + carry;
-    shifted_product<K>(q, c, true, r);
+    q[K] = m_sign + carry;
+    shifted_product<K>(q, c, true, X);
   } else {
     // q = (m >> n) + 2^alpha on K+1 limbs
-#pragma unroll U
-    for (int i = 0; i < K; ++i) q[i] = m[K + i];
-    q[K] = sign_mask(m[2 * K - 1]);
+    q[K] = m_sign;
     add_pow2<K, K + 1>(q, c.alpha);
-    shifted_product<K>(q, c, false, r);
+    shifted_product<K>(q, c, false, X);
   }
 }
 
@@ -376,38 +377,38 @@ __global__ void __launch_bounds__(256) limb_variant_kernel(const uint32_t* __res
   const bool is_signed = c.variant != MONT_PLANTARD;
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += stride) {
-    uint32_t T[2 * K];
+    uint32_t X[2 * K + 1], Y[3 * K + 1];
     if (mode == static_cast<int>(Mode::kRedc)) {
-      load_limbs<2 * K>(x + e * 2 * K, T, vec16);
+      load_limbs<2 * K>(x + e * 2 * K, X, vec16);
     } else {
-      uint32_t a[K];
+      uint32_t* a = Y;
+      uint32_t* b = Y + K;
       load_limbs<K>(x + e * K, a, vec16);
       if (mode == static_cast<int>(Mode::kFromDomain)) {
         const uint32_t ext = is_signed ? sign_mask(a[K - 1]) : 0u;
 #pragma unroll U
         for (int i = 0; i < K; ++i) {
-          T[i] = a[i];
-          T[K + i] = ext;
+          X[i] = a[i];
+          X[K + i] = ext;
         }
       } else {
-        uint32_t b[K];
         if (mode == static_cast<int>(Mode::kMul)) {
           load_limbs<K>(y + e * K, b, vec16);
         } else {
 #pragma unroll U
           for (int i = 0; i < K; ++i) b[i] = c.dom[i];
         }
-        mul_full<K, K, K>(a, b, T);
+        mul_full<K, K, K>(a, b, X);
         if (is_signed)                          // T mod 2^{64K} of the signed product
-          sub2_masked<K, K>(T + K, b, sign_mask(a[K - 1]), a, sign_mask(b[K - 1]));
+          sub2_masked<K, K>(X + K, b, sign_mask(a[K - 1]), a, sign_mask(b[K - 1]));
       }
     }
-    uint32_t r[K];
+    uint32_t* r = X + K;
     if (c.variant == MONT_SIGNED) {
-      sig_redc<K>(T, c, r);
+      sig_redc<K>(X, Y, c);
       if (mode == static_cast<int>(Mode::kFromDomain)) {
         // (-N, N) -> mods N: r > (N-1)/2 gives r - N, r < -(N-1)/2 gives r + N
-        uint32_t t[K];
+        uint32_t* t = Y;                        // m and m N are no longer needed
 #pragma unroll U
         for (int i = 0; i < K; ++i) t[i] = c.half[i];
         sub_masked<K, K>(t, r, 0xFFFFFFFFu);    // (N-1)/2 - r
@@ -420,9 +421,9 @@ __global__ void __launch_bounds__(256) limb_variant_kernel(const uint32_t* __res
         add_masked<K, K>(r, c.N, below);
       }
     } else if (c.variant == MONT_PLANTARD) {
-      p_redc<K>(T, c, r);
+      p_redc<K>(X, Y, c);
     } else {
-      sig_p_redc<K>(T, c, r);
+      sig_p_redc<K>(X, Y, c);
     }
     store_limbs<K>(out + e * K, r, vec16);
   }
