@@ -21,9 +21,10 @@
 // other factor times 2^{32j} is subtracted from the limbs it reaches.
 //
 // One thread per element, grid-stride.  Up to k = 16 the loops are fully
-// unrolled and the arrays live in registers; at k = 32 and 64 they live in
-// local memory and the products run over 16 x 16-limb register blocks.  The variant and the operation are uniform run-time
-// branches: one kernel per limb count.
+// unrolled and an element's state lives in registers; at k = 32 and 64 it
+// lives in local memory and the products run over 16 x 16-limb register
+// blocks.  The variant and the operation are uniform run-time branches: one
+// kernel per limb count.
 #include "internal.h"
 
 namespace montgb {
