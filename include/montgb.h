@@ -243,8 +243,10 @@ int mont_pipe_create(mont_pipe_t* out, size_t staging_bytes);
  * overlaps an input range or another output range in host memory, or if the
  * current device is not the pipe's; MONT_ENOMEM if one slot cannot hold
  * MONT_PIPE_MIN_CHUNK elements of every vector.  MONT_ECUDA if enqueueing
- * fails part-way (`stream` still waits for what was enqueued).  count = 0 is
- * a no-op.
+ * fails part-way, or the status of an operation's own mont_* call if that
+ * fails part-way: no further chunk is started, `stream` still waits for what
+ * was enqueued, and the host outputs of the run are unspecified.  count = 0
+ * is a no-op.
  */
 int mont_pipe_run(mont_pipe_t pipe, const mont_host_op* ops, int count, void* stream);
 
