@@ -329,15 +329,21 @@ def extra_rns64(mg, stream, peak):
 
 def extra_cios(mg, stream, peak):
     """Multi-limb REDC (CIOS), random odd N of 256/384/1024/2048 bits, operands
-    uniform in [0, N)."""
+    uniform in [0, N).  At 1024 and 2048 bits 2^17 and 2^15 drawn pairs are
+    tiled 8 times on the device (the kernel has no data-dependent branch), so
+    that the grid runs several waves."""
     import torch
     out = {}
-    for bits, count in ((256, 1 << 22), (384, 1 << 21), (1024, 1 << 17), (2048, 1 << 15)):
+    for bits, drawn, tile in ((256, 1 << 22, 1), (384, 1 << 21, 1), (1024, 1 << 17, 8),
+                              (2048, 1 << 15, 8)):
         k = bits // 32
+        count = drawn * tile
         N = sy.random_odd_modulus(bits, seed=4)
         ctx = mg.mont_ctx_create(N, bits, 0)
-        a = torch.from_numpy(sy.uniform_limb_residues(N, k, count, seed=40 + k).reshape(-1)).cuda()
-        b = torch.from_numpy(sy.uniform_limb_residues(N, k, count, seed=80 + k).reshape(-1)).cuda()
+        a = torch.from_numpy(
+            sy.uniform_limb_residues(N, k, drawn, seed=40 + k).reshape(-1)).cuda().repeat(tile)
+        b = torch.from_numpy(
+            sy.uniform_limb_residues(N, k, drawn, seed=80 + k).reshape(-1)).cuda().repeat(tile)
         o = torch.empty_like(a)
         L = mg.lib()
         sp = stream.cuda_stream
