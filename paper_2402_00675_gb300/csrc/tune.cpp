@@ -190,6 +190,14 @@ extern "C" int mont_autotune(mont_ctx_t ctx, size_t n, int flags, void* stream) 
             c.threads = th; c.unroll = u; c.vec_bytes = vb;
             cands.push_back(c);
           }
+    } else if (ctx->variant != MONT_REDC) {
+      // Algorithms 1-4 at multi-limb widths: one thread per element, so the
+      // block size is the only choice
+      for (int th : {128, 256}) {
+        LaunchShape c;
+        c.threads = th;
+        cands.push_back(c);
+      }
     } else {
       for (int team : {1, 2, 4, 8, 16})
         for (int th : {128, 256}) {

@@ -247,3 +247,27 @@ def test_launch_shapes_do_not_change_results(k):
             assert from_dev(out, k, True) == want, shape
     finally:
         mg.mont_tune_set(32 * k, variant, 0, None)
+
+
+def test_autotune_picks_a_block_size_and_keeps_results():
+    """mont_autotune on an Algorithm 2 context chooses between the two block
+    sizes (the kernel runs one thread per element: no lane teams); products
+    after tuning still equal the oracle's."""
+    k, variant = 8, mg.MONT_PLANTARD
+    rnd = random.Random(600)
+    l = 64 * k
+    N = moduli(variant, k, 1, rnd)[1]
+    ctx = mg.mont_ctx_create(N, l, variant, n_limbs=k)
+    try:
+        mg.mont_autotune(ctx, 1 << 14)
+        shape = mg.mont_tune_get(32 * k, variant, 0)
+        assert shape["threads"] in (128, 256) and shape["team"] == 0
+        cnt = 2000
+        a, b = operands(variant, N, cnt, rnd), operands(variant, N, cnt, rnd)
+        out = torch.zeros(cnt * k, dtype=torch.uint32, device="cuda")
+        mg.mont_mul(ctx, to_dev(a, k), to_dev(b, k), out, n=cnt)
+        torch.cuda.synchronize()
+        assert from_dev(out, k, False) == [o.mul_value(variant, x, y, N, l) for x, y in zip(a, b)]
+    finally:
+        for mode in range(4):
+            mg.mont_tune_set(32 * k, variant, mode, None)
