@@ -181,9 +181,13 @@ def test_argument_errors_need_no_gpu(L):
 
 def test_product_path_has_no_fallback(monkeypatch, tmp_path):
     """With the library missing the binding raises instead of computing."""
-    import importlib
-    monkeypatch.setattr(mg, "_lib", None)
+    import gc
+    # Finalizers of earlier tests' contexts call lib(); run them now, and point
+    # the path at the missing file before dropping the loaded handle, so that
+    # none can reload the real library in between.
+    gc.collect()
     monkeypatch.setattr(mg, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mg, "_lib", None)
     with pytest.raises(RuntimeError):
         mg.lib()
 
