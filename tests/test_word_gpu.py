@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import oracle as o
+from oracle import bulk
 import paper_2402_00675_gb300 as mg
 from gpu_helpers import (dev, dev_wide, empty_like_elems, host, input_range, log2R_of,
                          max_modulus, np_dtype, sync)
@@ -154,8 +155,8 @@ def test_ragged_sizes_alignment_and_in_place(variant, width):
 
 
 def test_full_size_redc32_2p20():
-    """REDC, R = 2^32, N = 3329, 2^20 pairs uniform in [0, N): sampled parity
-    plus the range property on every element."""
+    """REDC, R = 2^32, N = 3329, 2^20 pairs uniform in [0, N): every element
+    against the definition T R^{-1} mod N."""
     import synthetic as sy
     N, n = sy.REDC32_N, 1 << 20
     a = sy.uniform_residues(N, n, seed=1)
@@ -164,19 +165,21 @@ def test_full_size_redc32_2p20():
     out = torch.empty(n, dtype=torch.uint32, device="cuda")
     mg.mont_mul(ctx, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), out)
     sync()
-    got = out.cpu().numpy()
-    assert int(got.max()) < N
-    rnd = random.Random(5)
-    idx = list(range(2000)) + list(range(n - 2000, n)) + [rnd.randrange(n) for _ in range(20000)]
-    for i in idx:
-        assert int(got[i]) == o.mul_value(0, int(a[i]), int(b[i]), N, 32), i
+    got = out.cpu().numpy().astype(np.int64)
+    want = bulk.mul_value_u32(0, a, b, N, 32)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (bad[:10], got[bad[:10]], want[bad[:10]])
+    # the whole-array oracle agrees with the scalar definition where it is cheap
+    for i in (0, 1, n // 2, n - 1):
+        assert int(want[i]) == o.mul_value(0, int(a[i]), int(b[i]), N, 32)
 
 
 @pytest.mark.parametrize("N", [3329, 8380417])
 def test_full_size_word32_variants_2p26(N):
     """The 2^26-pair workload of the signed and Plantard variants, as the
-    benchmark launches it: sampled element parity plus the claimed range of
-    every element."""
+    benchmark launches it: every element of every output against the
+    definition (Algorithm 1: its representative (T - mN)/R; Algorithms 2-4:
+    -T R^{-1} mod N, mods N for the signed ones)."""
     import synthetic as sy
     n = 1 << 26
     a = sy.centred_residues(N, n, seed=2 * N + 1)
@@ -184,8 +187,6 @@ def test_full_size_word32_variants_2p26(N):
     au, bu = sy.lift_unsigned(a, N), sy.lift_unsigned(b, N)
     da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
     dau, dbu = torch.from_numpy(au).cuda(), torch.from_numpy(bu).cuda()
-    rnd = random.Random(N)
-    idx = list(range(1000)) + list(range(n - 1000, n)) + [rnd.randrange(n) for _ in range(8000)]
     for variant, l in ((1, 32), (2, 64), (3, 64), (4, 64)):
         ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
         signed = variant != 2
@@ -196,8 +197,11 @@ def test_full_size_word32_variants_2p26(N):
             mg.mont_mul(ctx, dau, dbu, out)
         sync()
         got = out.cpu().numpy().astype(np.int64)
+        xa, xb = (a, b) if signed else (au, bu)
+        want = bulk.mul_value_u32(variant, xa, xb, N, l, 1)
+        bad = np.flatnonzero(got != want)
+        assert bad.size == 0, (variant, bad[:10], got[bad[:10]], want[bad[:10]])
         lo, hi = o.claimed_range(variant, N)
         assert got.min() >= lo and got.max() <= hi
-        xa, xb = (a, b) if signed else (au, bu)
-        for i in idx:
-            assert int(got[i]) == o.mul_value(variant, int(xa[i]), int(xb[i]), N, l, 1), (variant, i)
+        for i in (0, n - 1):
+            assert int(want[i]) == o.mul_value(variant, int(xa[i]), int(xb[i]), N, l, 1)
