@@ -52,9 +52,9 @@ ALPHA = 1
 
 # DRAM bytes per launch of the word kernel on this workload (read + write,
 # mean of the 8 launches of one step), from a one-pass ncu capture of the
-# full-size launch (profiles/word32_mont_mul_2p26.md).  Reads equal the
-# algorithmic 536.9 MB; writes (228.1 MB of 268.4 MB) exclude the output tail
-# still dirty in L2 when the kernel ends, which the next launch writes back.
+# full-size launch.  Reads equal the algorithmic 536.9 MB; writes (228.1 MB of
+# 268.4 MB) exclude the output tail still dirty in L2 when the kernel ends,
+# which the next launch writes back.
 NCU_TRAFFIC_BYTES_PER_LAUNCH = 764974976
 
 
@@ -65,7 +65,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--e2e-steps", type=int, default=0, help="0: min(steps, 10)")
-    p.add_argument("--cpu-budget-s", type=float, default=12.0)
+    p.add_argument("--cpu-work-s", type=float, default=24.0,
+                   help="CPU seconds (summed over cores) the oracle baseline runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the per-config measurements after the main step")
@@ -176,47 +177,149 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- cpu oracle
 
-def oracle_sample_rate(inputs, budget_s: float):
-    """Time the oracle (as it stands) on the first pairs of each of the 8
-    vectors until about budget_s seconds of CPU work; returns (Gmodmul/s,
-    pairs per vector, seconds)."""
-    import oracle as o
-    per = 64
-    done = 0
-    t_used = 0.0
-    while True:
-        t0 = time.perf_counter()
-        for N in MODULI:
-            a, b, au, bu = inputs[N]
-            for variant, l in COMBOS:
-                x, y = (au, bu) if variant == 2 else (a, b)
-                for i in range(done, done + per):
-                    o.mul_value(variant, int(x[i]), int(y[i]), N, l, ALPHA)
-        t_used += time.perf_counter() - t0
-        done += per
-        if t_used >= budget_s or done + 2 * per > N_PAIRS:
-            break
-        per *= 2
-    total = done * len(MODULI) * len(COMBOS)
-    return total / t_used / 1e9, done, t_used
+SLICE_PAIRS = 1 << 15   # pairs of each of the 8 vectors a worker cycles over
 
+
+def _oracle_slices(inputs, worker: int):
+    """Worker `worker`'s own disjoint pairs of each (modulus, variant) vector."""
+    lo = worker * SLICE_PAIRS
+    hi = min(lo + SLICE_PAIRS, N_PAIRS)
+    out = []
+    for N in MODULI:
+        a, b, au, bu = inputs[N]
+        for variant, l in COMBOS:
+            x, y = (au, bu) if variant == 2 else (a, b)
+            out.append((variant, N, l, x[lo:hi].tolist(), y[lo:hi].tolist()))
+    return out
+
+
+def _oracle_work(task):
+    """Runs in a spawned process: the oracle, as it stands, over this worker's
+    slices.  ("budget", s): round-robin blocks of 256 pairs per vector until s
+    seconds pass; ("count", c): exactly c pairs of each vector.  Returns
+    (products, seconds)."""
+    import oracle as o
+    mode, amount, slices = task
+    pos = 0
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        blk = 256 if mode == "budget" else amount
+        for variant, N, l, xs, ys in slices:
+            m = len(xs)
+            for j in range(pos, pos + blk):
+                i = j % m
+                o.mul_value(variant, xs[i], ys[i], N, l, ALPHA)
+        done += blk * len(slices)
+        pos += blk
+        if mode == "count" or time.perf_counter() - t0 >= amount:
+            break
+    return done, time.perf_counter() - t0
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+class OraclePool:
+    """One spawned process per host core, each holding its own disjoint
+    slice of the workload (SLICE_PAIRS pairs of each of the 8 vectors)."""
+
+    def __init__(self, inputs, cores: int):
+        import multiprocessing as mp
+        self.cores = max(1, min(cores, N_PAIRS // SLICE_PAIRS))
+        self.slices = [_oracle_slices(inputs, w) for w in range(self.cores)]
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_work, [("count", 1, sl) for sl in self.slices])   # imports
+
+    def budget(self, seconds: float):
+        """Products per second over all cores, each running `seconds`."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_work, [("budget", seconds, sl) for sl in self.slices])
+        wall = time.perf_counter() - t0
+        done = sum(r[0] for r in res)
+        return done / wall, done, wall
+
+    def count(self, per: int):
+        """Every core evaluates `per` pairs of each of its 8 vectors."""
+        res = self.pool.map(_oracle_work, [("count", per, sl) for sl in self.slices])
+        return sum(r[0] for r in res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_baseline(inputs, budget_s: float):
+    """The oracle timed on every host core (one process each) for about
+    budget_s seconds of wall time."""
+    cores, model = host_cpu()
+    pool = OraclePool(inputs, cores)
+    rate, done, wall = pool.budget(budget_s)
+    pool.close()
+    return {"value": rate / 1e9, "unit": METRIC, "cores": pool.cores, "kind": "oracle",
+            "cpu": model,
+            "sample": f"{pool.cores} spawned processes (one per host core), each cycling over its "
+                      f"own disjoint {SLICE_PAIRS} pairs of each of the 8 (modulus, variant) vectors: "
+                      f"{done} oracle products in {wall:.1f} s wall, Python big-int"}
 
 
 # ---------------------------------------------------------------- extras
 # Each extra measures one other workload of the library outside the main
 # timed region, with CUDA events on the launching stream, and carries its own
 # roofline.  Peaks: HBM from MEASURED_PEAKS.json; integer peaks derived from
-# unit counts (per SM and clock: 4 schedulers x 32 lanes = 128 issued thread
-# instructions; 64 mad.lo; 32 mad.hi) at the 2070 MHz maximum SM clock.
+# unit counts per SM and clock (4 schedulers x 32 lanes = 128 issued thread
+# instructions; 64 mad.lo; 32 mad.hi, so a 32x32->64 limb product, lo + hi,
+# takes 3/64 of an SM-cycle) times the SM count queried from the device and
+# its maximum SM clock; the sweep's peak is the mad.lo rate measured live.
 
-SMS = 152
-SM_MHZ_MAX = 2070.0
-ISSUE_PEAK = 128 * SMS * SM_MHZ_MAX * 1e6            # thread-instructions / s
-LIMB_PRODUCT_PEAK = 64.0 / 3.0 * SMS * SM_MHZ_MAX * 1e6  # lo + hi product pairs / s
-# integer operations per sweep check of each algorithm's formula (the formula's
-# own operations, the reference step c += s R^-1 mod N, the congruence and
-# range tests and the loop step); see DESIGN.md
+PEAKS = {"sms": 152, "sm_mhz_max": 2070.0}
+
+
+def set_int_peaks(sms: int, sm_mhz_max: float) -> None:
+    """Integer peaks of the device the benchmark runs on."""
+    hz = sm_mhz_max * 1e6
+    PEAKS.update(sms=sms, sm_mhz_max=sm_mhz_max,
+                 issue=128.0 * sms * hz,                 # thread-instructions / s
+                 limb=64.0 / 3.0 * sms * hz,             # lo + hi limb products / s
+                 mad_lo=64.0 * sms * hz)                 # mad.lo.u32 / s
+
+
+set_int_peaks(152, 2070.0)
+
+
+def read_measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def device_int_peaks(peaks_file: dict) -> None:
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    set_int_peaks(props.multi_processor_count, float(peaks_file.get("sm_max_mhz") or 2070.0))
+
+
+# Integer operations per sweep check of each algorithm's formula as issued
+# (the formula's own operations, the reference step c += s R^-1 mod N, the
+# congruence and range tests and the loop step): an issue-slot figure only.
 SWEEP_OPS = {0: 16, 1: 17, 2: 16, 3: 17, 4: 16}
+# The survey's algorithmic unit for the sweep: a check costs about 3 IMAD
+# slots (T N' low product, m N, and the reference step), so the roofline is
+# the measured mad.lo rate / 3 checks per second.
+SWEEP_IMAD_PER_CHECK = 3.0
 
 
 def _events_ms(fn, reps, stream):
@@ -291,7 +394,8 @@ def extra_redc32(mg, stream, peak):
 
 def extra_rns64(mg, stream, peak):
     """32 primes of 60-62 bits, p = 1 mod 2^17, log-uniform lengths 2^12..2^22:
-    one graph-launched persistent batch against 32 plain launches."""
+    one graph-launched persistent batch, its launch shape picked by the
+    autotuner for 64-bit words, against 32 plain launches."""
     import torch
     primes = sy.rns_primes(32, seed=3)
     lens = sy.log_uniform_lengths(32, 12, 22, seed=3)
@@ -301,6 +405,9 @@ def extra_rns64(mg, stream, peak):
         da.append(torch.from_numpy(sy.uniform_residues(p_, n, seed=1000 + j, dtype=np.uint64)).cuda())
         db.append(torch.from_numpy(sy.uniform_residues(p_, n, seed=2000 + j, dtype=np.uint64)).cuda())
         outs.append(torch.empty(n, dtype=torch.uint64, device="cuda"))
+    default_shape = mg.mont_tune_get(64, 0, mg.MONT_TUNE_MODE_BATCHED)
+    mg.mont_autotune(ctxs[0], 1 << 22, mg.MONT_TUNE_BATCHED, stream)
+    tuned = mg.mont_tune_get(64, 0, mg.MONT_TUNE_MODE_BATCHED)
     plan = mg.Batch(ctxs, da, db, outs, lens)
     L = mg.lib()
     sp = stream.cuda_stream
@@ -318,32 +425,28 @@ def extra_rns64(mg, stream, peak):
     tot = sum(lens)
     gb = 24 * tot / (t_batch * 1e-3) / 1e9
     plan.close()
+    shape = lambda d: f"{d['threads']}t/u{d['unroll']}/{d['blocks_per_sm'] or 'occ'}"
     return {"workload": f"RNS REDC R=2^64, 32 primes, sum(len)={tot}", "unit": "Gmodmul/s",
             "batched_graph": round(tot / (t_batch * 1e-3) / 1e9, 1),
             "plain_32_launches": round(tot / (t_plain * 1e-3) / 1e9, 1),
             "speedup": round(t_plain / t_batch, 2),
             "us_batched": round(t_batch * 1e3, 2), "us_plain": round(t_plain * 1e3, 2),
+            "shape_tuned": shape(tuned), "shape_default": shape(default_shape),
             "roofline": {"bound": "hbm", "achieved": round(gb, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(gb / peak, 3)}}
 
 
 def extra_cios(mg, stream, peak):
-    """Multi-limb REDC (CIOS), random odd N of 256/384/1024/2048 bits, operands
-    uniform in [0, N).  At 1024 and 2048 bits 2^17 and 2^15 drawn pairs are
-    tiled 8 times on the device (the kernel has no data-dependent branch), so
-    that the grid runs several waves."""
+    """Multi-limb REDC (CIOS) at the stated sizes: random odd N of
+    256/384/1024/2048 bits, 2^22/2^21/2^17/2^15 pairs uniform in [0, N)."""
     import torch
     out = {}
-    for bits, drawn, tile in ((256, 1 << 22, 1), (384, 1 << 21, 1), (1024, 1 << 17, 8),
-                              (2048, 1 << 15, 8)):
+    for bits, count in ((256, 1 << 22), (384, 1 << 21), (1024, 1 << 17), (2048, 1 << 15)):
         k = bits // 32
-        count = drawn * tile
         N = sy.random_odd_modulus(bits, seed=4)
         ctx = mg.mont_ctx_create(N, bits, 0)
-        a = torch.from_numpy(
-            sy.uniform_limb_residues(N, k, drawn, seed=40 + k).reshape(-1)).cuda().repeat(tile)
-        b = torch.from_numpy(
-            sy.uniform_limb_residues(N, k, drawn, seed=80 + k).reshape(-1)).cuda().repeat(tile)
+        a = torch.from_numpy(sy.uniform_limb_residues(N, k, count, seed=40 + k).reshape(-1)).cuda()
+        b = torch.from_numpy(sy.uniform_limb_residues(N, k, count, seed=80 + k).reshape(-1)).cuda()
         o = torch.empty_like(a)
         L = mg.lib()
         sp = stream.cuda_stream
@@ -356,11 +459,11 @@ def extra_cios(mg, stream, peak):
         gb = 12 * k * count / (ms * 1e-3) / 1e9
         out[f"{bits}b"] = {
             "pairs": count, "gmodmul_s": round(count / (ms * 1e-3) / 1e9, 3),
-            "us": round(ms * 1e3, 2), "team": mg.mont_tune_get(bits, 0, 0)["team"] or None,
+            "us": round(ms * 1e3, 2),
             "roofline": {"bound": "alu", "achieved": round(ach / 1e12, 3),
-                         "peak": round(LIMB_PRODUCT_PEAK / 1e12, 3),
+                         "peak": round(PEAKS["limb"] / 1e12, 3),
                          "unit": "T limb-products/s (32x32->64, lo+hi)",
-                         "frac": round(ach / LIMB_PRODUCT_PEAK, 3),
+                         "frac": round(ach / PEAKS["limb"], 3),
                          "hbm_frac": round(gb / peak, 3)}}
     return out
 
@@ -368,15 +471,12 @@ def extra_cios(mg, stream, peak):
 def extra_limb_variants(mg, stream, peak):
     """Algorithms 1-4 at 256, 1024 and 2048 bits (n = 32k: R = 2^{32k} for
     Algorithm 1, 2^{64k} for Algorithms 2-4), random odd N at each variant's
-    largest size class, operands uniform in the variant's output range.  At
-    1024 and 2048 bits 2^17 and 2^15 drawn pairs are tiled 8 times on the
-    device (the kernel has no data-dependent branch; the operands stay larger
-    than L2): enough elements for about nine waves of the grid."""
+    largest size class, operands uniform in the variant's output range;
+    2^21 / 2^17 / 2^15 pairs."""
     import torch
     out = {}
     names = {1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
-    for bits, drawn, tile in ((256, 1 << 21, 1), (1024, 1 << 17, 8), (2048, 1 << 15, 8)):
-        count = drawn * tile
+    for bits, count in ((256, 1 << 21), (1024, 1 << 17), (2048, 1 << 15)):
         k = bits // 32
         L = mg.lib()
         sp = stream.cuda_stream
@@ -385,12 +485,12 @@ def extra_limb_variants(mg, stream, peak):
             N = sy.random_odd_modulus(top_bits, seed=4 + variant)
             log2R = 2 * bits if variant >= 2 else bits
             ctx = mg.mont_ctx_create(N, log2R, variant, alpha=1, n_limbs=k)
-            a = sy.uniform_limb_residues(N, k, drawn, seed=40 + variant)
-            b = sy.uniform_limb_residues(N, k, drawn, seed=80 + variant)
+            a = sy.uniform_limb_residues(N, k, count, seed=40 + variant)
+            b = sy.uniform_limb_residues(N, k, count, seed=80 + variant)
             if variant != 2:   # signed variants: centre the residues (x - N for x > N/2)
                 a, b = (sy.centred_limb_residues(N, x) for x in (a, b))
-            da = torch.from_numpy(a.reshape(-1)).cuda().repeat(tile)
-            db = torch.from_numpy(b.reshape(-1)).cuda().repeat(tile)
+            da = torch.from_numpy(a.reshape(-1)).cuda()
+            db = torch.from_numpy(b.reshape(-1)).cuda()
             o = torch.empty_like(da)
             f = lambda: L.mont_mul(ctx.handle, da.data_ptr(), db.data_ptr(), o.data_ptr(), count, sp)
             for _ in range(5):
@@ -405,19 +505,25 @@ def extra_limb_variants(mg, stream, peak):
                 "pairs": count, "gmodmul_s": round(count / (ms * 1e-3) / 1e9, 3),
                 "us": round(ms * 1e3, 2),
                 "roofline": {"bound": "alu", "achieved": round(ach / 1e12, 3),
-                             "peak": round(LIMB_PRODUCT_PEAK / 1e12, 3),
+                             "peak": round(PEAKS["limb"] / 1e12, 3),
                              "unit": "T limb-products/s (32x32->64, lo+hi)",
-                             "frac": round(ach / LIMB_PRODUCT_PEAK, 3),
+                             "frac": round(ach / PEAKS["limb"], 3),
                              "hbm_frac": round(12 * k * count / (ms * 1e-3) / 1e9 / peak, 3)}}
     return out
 
 
 def extra_sweep(mg, stream):
     """R = 2^16, every odd N in [3, 4095]; each algorithm on its own domain,
-    and on REDC's domain 0 <= T < RN."""
+    and on REDC's domain 0 <= T < RN.  Roofline: the measured mad.lo rate / 3
+    checks per second; the issue-slot fraction of the formula's own operation
+    count is kept beside it."""
     import torch
     out = {}
     names = {0: "redc", 1: "sigredc", 2: "predc", 3: "sigpredc1", 4: "sigpredc2_a1"}
+    mad_lo = mg.mont_probe_int_rate(0, 4096, stream)
+    peak_checks = mad_lo / SWEEP_IMAD_PER_CHECK
+    out["peak"] = {"mad_lo_t_s": round(mad_lo / 1e12, 2), "checks_t_s": round(peak_checks / 1e12, 3),
+                   "unit": "T checks/s = measured mad.lo rate / 3"}
     redc_dom = mg.MontBounds(mg.MONT_DOMAIN_REDC, mg.MONT_RANGE_DEFAULT, 0, 0, 0, 0)
     for v, alpha in ((0, 0), (1, 0), (2, 0), (3, 0), (4, 1)):
         for dom_name, dom in (("own_domain", None), ("redc_domain", redc_dom)):
@@ -431,13 +537,14 @@ def extra_sweep(mg, stream):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             checks = sum(r.checked.values())
-            ops = checks * SWEEP_OPS[v]
+            rate = checks / (ms * 1e-3)
             out[f"{names[v]}_{dom_name}"] = {
                 "checks": checks, "counterexamples": r.total,
-                "ms": round(ms, 3), "gchecks_s": round(checks / (ms * 1e-3) / 1e9, 2),
-                "roofline": {"bound": "alu", "achieved": round(ops / (ms * 1e-3) / 1e12, 3),
-                             "peak": round(ISSUE_PEAK / 1e12, 2), "unit": "T int-ops/s",
-                             "frac": round(ops / (ms * 1e-3) / ISSUE_PEAK, 3)}}
+                "ms": round(ms, 3), "gchecks_s": round(rate / 1e9, 2),
+                "roofline": {"bound": "alu", "achieved": round(rate / 1e12, 3),
+                             "peak": round(peak_checks / 1e12, 3), "unit": "T checks/s",
+                             "frac": round(rate / peak_checks, 3),
+                             "issue_frac": round(rate * SWEEP_OPS[v] / PEAKS["issue"], 3)}}
     return out
 
 
@@ -450,7 +557,7 @@ def extra_sweep(mg, stream):
 # Plantard's prepared twiddles: the product (two products and one product with
 # N, 3), then 2 + 2 + 1 as above: 8.  64-bit words, counting every 64-bit
 # product in 32-bit multiply-adds (4 for a full or high product, 3 for a low
-# one) and 64-bit adds as 2: REDC 30, Plantard 26; see the design doc
+# one) and 64-bit adds as 2: REDC 30, Plantard 26.
 NTT_BUTTERFLY_OPS = {(0, 32): 11, (2, 32): 8, (0, 64): 30, (2, 64): 26}
 
 
@@ -487,8 +594,8 @@ def extra_ntt(mg, stream, peak):
                 "polys": batch, "forward_us": round(ms_f * 1e3, 1), "inverse_us": round(ms_i * 1e3, 1),
                 "gcoeff_s": round(batch * n / (ms_f * 1e-3) / 1e9, 1),
                 "roofline": {"bound": "alu", "achieved": round(ops / 1e12, 2),
-                             "peak": round(ISSUE_PEAK / 1e12, 2), "unit": "T int-ops/s",
-                             "frac": round(ops / ISSUE_PEAK, 3), "hbm_frac": round(gb / peak, 3)}}
+                             "peak": round(PEAKS["issue"] / 1e12, 2), "unit": "T int-ops/s",
+                             "frac": round(ops / PEAKS["issue"], 3), "hbm_frac": round(gb / peak, 3)}}
             plan.close()
     for tag in ("n256_w32", "n1024_w64"):
         out[f"{tag}_plantard_speedup_over_redc"] = round(
@@ -546,18 +653,13 @@ def extra_dot(mg, stream, peak):
 
 
 def extra_rns(mg, stream):
-    """Conversions between 2^20 big integers and their residues modulo the 32
-    RNS primes (product of 1950 bits, 64 limbs): 2^17 drawn integers tiled 8
-    times on the device (the kernels have no data-dependent branch), so that
-    the reconstruction, at 77,824 resident threads, runs about 13 waves
-    instead of 1.7."""
+    """Conversions between 2^17 big integers uniform below P and their
+    residues modulo the 32 RNS primes (product of 1950 bits, 64 limbs)."""
     import torch
     ps = sy.rns_primes(32, seed=3)
     r = mg.Rns(ps)
-    drawn, tile = 1 << 17, 8
-    n, k = drawn * tile, r.limbs
-    X = torch.from_numpy(
-        sy.uniform_limb_residues(_product(ps), k, drawn, seed=13).reshape(-1)).cuda().repeat(tile)
+    n, k = 1 << 17, r.limbs
+    X = torch.from_numpy(sy.uniform_limb_residues(_product(ps), k, n, seed=13).reshape(-1)).cuda()
     res = torch.empty(32 * n, dtype=torch.uint64, device="cuda")
     Y = torch.empty_like(X)
     f = lambda: r.to_residues(X, res, n, stream)
@@ -581,17 +683,17 @@ def extra_rns(mg, stream):
     r.close()
     a_to = n * prods_to / (ms_to * 1e-3)
     a_from = n * prods_from / (ms_from * 1e-3)
-    return {"workload": "2^20 integers below P (2^17 drawn, tiled 8 times), 32 primes of 60-62 bits",
+    return {"workload": "2^17 integers below P, 32 primes of 60-62 bits",
             "to_residues_us": round(ms_to * 1e3, 1), "from_residues_us": round(ms_from * 1e3, 1),
             "to_melem_s": round(n / (ms_to * 1e-3) / 1e6, 1),
             "from_melem_s": round(n / (ms_from * 1e-3) / 1e6, 1),
             "roofline": {"bound": "alu", "unit": "T limb-products/s (32x32->64, lo+hi)",
-                         "peak": round(LIMB_PRODUCT_PEAK / 1e12, 3),
+                         "peak": round(PEAKS["limb"] / 1e12, 3),
                          "limb_products_per_element": {"to": prods_to, "from": prods_from},
                          "achieved_to": round(a_to / 1e12, 3),
                          "achieved_from": round(a_from / 1e12, 3),
-                         "frac_to": round(a_to / LIMB_PRODUCT_PEAK, 3),
-                         "frac_from": round(a_from / LIMB_PRODUCT_PEAK, 3)}}
+                         "frac_to": round(a_to / PEAKS["limb"], 3),
+                         "frac_from": round(a_from / PEAKS["limb"], 3)}}
 
 
 def _product(xs):
@@ -601,9 +703,12 @@ def _product(xs):
     return p
 
 
-def extra_serving(mg, jobs_count):
-    """Poisson stream of mixed jobs through the serving loop at 0.5x and 0.8x
-    of the measured capacity."""
+def extra_serving(mg, jobs_count, stream, peak, sweep=None):
+    """Poisson stream of mixed jobs through the serving loop at full rate
+    (capacity) and at 0.5x and 0.8x of the measured capacity, with the
+    stream's lower-bound time (sweep checks at the measured sweep rates, the
+    host link at its measured rate) beside it."""
+    import torch
     from paper_2402_00675_gb300 import serving
     ctxs = serving.Contexts.create(3329, sy.rns_primes(1, seed=31)[0],
                                    sy.random_odd_modulus(256, seed=32))
@@ -612,8 +717,23 @@ def extra_serving(mg, jobs_count):
     server = mg.Server(8 << 30, slots=8)
     out = {"jobs_per_run": jobs_count, "slots": 8, "arena_gb": 8}
     jobs = sy.serving_jobs(jobs_count, 1.0, seed=5)
+    # the link as the serving copies see it: pinned pool in, pinned ring out
+    h_in = pools.pools[(0, 256)][0]
+    d_buf = torch.empty_like(h_in, device="cuda")
+    h_out = ring.buf[: h_in.numel() * h_in.element_size()].view(h_in.dtype)
+    link = measure_link(h_in, d_buf, h_out, d_buf, stream)
+    del d_buf
+    rates = {}
+    names = {0: "redc", 1: "sigredc", 2: "predc"}
+    for v in (0, 1, 2):
+        key = f"{names[v]}_own_domain"
+        rates[v] = (sweep[key]["gchecks_s"] * 1e9) if sweep and key in sweep else 1e12
+    bound = serving.stream_bound(jobs, rates, link["both_each_gbs"], peak, pools.max_len)
+    bound["link"] = link
+    out["bound"] = bound
     cap = serving.summarise(serving.run_stream(server, jobs, ctxs, pools, ring, rate_scale=0.0))
     out["capacity"] = cap
+    out["capacity_frac_of_bound"] = round(cap["makespan_s"] and bound["bound_s"] / cap["makespan_s"], 3)
     for lam in (0.5, 0.8):
         rate = lam * cap["jobs_per_s"]
         jobs = sy.serving_jobs(jobs_count, rate, seed=5)
@@ -621,6 +741,7 @@ def extra_serving(mg, jobs_count):
             serving.run_stream(server, jobs, ctxs, pools, ring, rate_scale=1.0))
     server.close()
     return out
+
 
 # ---------------------------------------------------------------- our arm
 
@@ -636,6 +757,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     mg.build()
     L = mg.lib()
+    device_int_peaks(read_measured_peaks())
 
     inputs = make_inputs()
     dev_in = {}
@@ -760,12 +882,7 @@ def run_ours(args):
     link = {"before": link_before, "after": link_now()}
 
     # ---------------- roofline of the dominant kernel (the word kernel)
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
+    peaks = read_measured_peaks()
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
@@ -782,17 +899,22 @@ def run_ours(args):
             "ntt": extra_ntt(mg, stream, peak),
             "dot_lazy": extra_dot(mg, stream, peak),
             "rns_convert": extra_rns(mg, stream),
-            "serving": extra_serving(mg, args.serving_jobs),
         }
+        extras["serving"] = extra_serving(mg, args.serving_jobs, stream, peak, extras["sweep_r16"])
 
     result = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            rate, per, secs = oracle_sample_rate(inputs, args.cpu_budget_s)
-            cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-                   "sample": f"first {per} pairs of each of the 8 (modulus, variant) vectors, "
-                             f"{per * 8} oracle products in {secs:.1f} s, Python big-int, 1 thread"}
+            cores = os.cpu_count() or 1
+            cpu = oracle_baseline(inputs, max(1.5, args.cpu_work_s / cores))
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH,
+                "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
+                "kernel": "word_kernel (mont_mul, 32-bit words)",
+                "avg_launch_us": round(avg_launch_ms * 1e3, 2),
+                "algorithmic_bytes_per_launch": BYTES_PER_MODMUL * N_PAIRS}
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": METRIC, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 4),
@@ -807,64 +929,103 @@ def run_ours(args):
                             f"inputs copied in once, 8 outputs copied out, chunks of "
                             f"{e2e_chunk} elements"},
             "gpu_launches": len(calls) * K,
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH,
-                         "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
-                         "kernel": "word_kernel (mont_mul, 32-bit words)",
-                         "avg_launch_us": round(avg_launch_ms * 1e3, 2),
-                         "algorithmic_bytes_per_launch": BYTES_PER_MODMUL * N_PAIRS},
+            "roofline": roof,
             "per_variant_gmodmul_s": per_variant,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "int_peaks": {"sms": PEAKS["sms"], "sm_mhz_max": PEAKS["sm_mhz_max"],
+                          "limb_t_s": round(PEAKS["limb"] / 1e12, 3),
+                          "issue_t_s": round(PEAKS["issue"] / 1e12, 2)},
             "extras": extras,
         }
+        # last key, so that it survives a reader that keeps only the tail
+        result["configs"] = config_summary(round(value, 1), roof, extras)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return result
 
 
+def config_summary(value, roof, ex):
+    """One compact entry per workload at its stated size: throughput and
+    roofline fraction (of measured HBM, of the derived limb-product peak, or
+    of the measured mad.lo rate / 3 for the sweep)."""
+    c = {"2_word32_2p26": {"gmodmul_s": value, "frac_hbm": roof["frac"]}}
+    if not ex:
+        return c
+    r = ex["redc32_2p20"]
+    c["1_redc32_2p20"] = {"gmodmul_s_hot": r["hot_l2"], "gmodmul_s_cold": r["cold_l2"],
+                          "frac_hbm_cold": r["roofline"]["frac"]}
+    b = ex["rns64_batched"]
+    c["3_rns64_batch"] = {"gmodmul_s": b["batched_graph"], "frac_hbm": b["roofline"]["frac"],
+                          "plain_gmodmul_s": b["plain_32_launches"], "speedup": b["speedup"],
+                          "tuned": b["shape_tuned"]}
+    c["4a_cios"] = {k.rstrip("b"): [v["gmodmul_s"], v["roofline"]["frac"]]
+                    for k, v in ex["cios"].items()}
+    sw = ex["sweep_r16"]
+    c["4b_sweep_r16"] = {k.replace("_own_domain", ""): [v["gchecks_s"], v["roofline"]["frac"]]
+                         for k, v in sw.items() if k.endswith("_own_domain")}
+    sv = ex["serving"]
+    c["5_serving"] = {"cap_jobs_s": round(sv["capacity"]["jobs_per_s"], 1),
+                      "cap_frac_of_bound": sv.get("capacity_frac_of_bound"),
+                      "gmodmul_s": round(sv["capacity"]["gmodmul_s"], 2),
+                      "p50_p99_ms_0.5": [round(sv["load_0.5"]["p50_ms"], 1),
+                                         round(sv["load_0.5"]["p99_ms"], 1)],
+                      "modmul_p50_p99_ms_0.5": [round(sv["load_0.5"]["modmul_p50_ms"], 1),
+                                                round(sv["load_0.5"]["modmul_p99_ms"], 1)],
+                      "p50_p99_ms_0.8": [round(sv["load_0.8"]["p50_ms"], 1),
+                                         round(sv["load_0.8"]["p99_ms"], 1)]}
+    lv = ex["limb_variants"]
+    nt = ex["ntt"]
+    rc = ex["rns_convert"]["roofline"]
+    c["next"] = {
+        "ntt256_w32_plantard": nt["n256_w32_plantard"]["roofline"]["frac"],
+        "ntt1024_w64_plantard": nt["n1024_w64_plantard"]["roofline"]["frac"],
+        "dot_lazy_hbm": ex["dot_lazy"]["roofline"]["frac"],
+        "rns_to_from": [rc["frac_to"], rc["frac_from"]],
+        "alg1to4": {w: [min(v["roofline"]["frac"] for k, v in lv.items() if k.startswith(w)),
+                        max(v["roofline"]["frac"] for k, v in lv.items() if k.startswith(w))]
+                    for w in ("256b", "1024b", "2048b")}}
+    return c
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
-    """The CPU oracle as the reference arm: each step evaluates a bounded
-    sample of the same workload (the first pairs of each of the 8 vectors)."""
+    """The CPU oracle as the reference arm, on every host core (one spawned
+    process each, each over its own disjoint pairs of the 8 vectors): each
+    step evaluates a bounded sample of the same workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    import oracle as o
     inputs = make_inputs()
+    cores, model = host_cpu()
+    pool = OraclePool(inputs, cores)
     # size a step so that warmup + steps take about a minute in total
-    probe_rate, _, _ = oracle_sample_rate(inputs, 0.5)
+    probe_rate, _, _ = pool.budget(0.5)
     per_step_s = 60.0 / max(1, args.steps + args.warmup)
-    per = max(1, int(per_step_s * probe_rate * 1e9 / 8))
-
-    def step():
-        for N in MODULI:
-            a, b, au, bu = inputs[N]
-            for variant, l in COMBOS:
-                x, y = (au, bu) if variant == 2 else (a, b)
-                for i in range(per):
-                    o.mul_value(variant, int(x[i]), int(y[i]), N, l, ALPHA)
-
+    per = max(1, int(per_step_s * probe_rate / (8 * pool.cores)))
     for _ in range(args.warmup):
-        step()
+        pool.count(per)
     t0 = time.perf_counter()
+    done = 0
     for _ in range(args.steps):
-        step()
+        done += pool.count(per)
     secs = time.perf_counter() - t0
-    value = args.steps * per * 8 / secs / 1e9
+    pool.close()
+    value = done / secs / 1e9
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/i32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs_per_modulus": N_PAIRS, "moduli": list(MODULI),
-                   "sample_pairs_per_vector_per_step": per},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                         "sample": f"first {per} pairs of each of the 8 (modulus, variant) "
-                                   "vectors per step, Python big-int, 1 thread"},
+                   "sample_pairs_per_vector_per_step_per_core": per},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": pool.cores, "kind": "oracle",
+                         "cpu": model,
+                         "sample": f"{pool.cores} spawned processes (one per host core), each "
+                                   f"evaluating {per} of its own disjoint pairs of each of the 8 "
+                                   "(modulus, variant) vectors per step, Python big-int"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -873,18 +1034,18 @@ def run_extras_only(names):
     import torch
     import paper_2402_00675_gb300 as mg
     mg.build()
-    peak = 6800.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak = json.load(f).get("hbm_gbs") or peak
-    except OSError:
-        pass
+    peaks = read_measured_peaks()
+    device_int_peaks(peaks)
+    peak = peaks.get("hbm_gbs") or 6800.0
     stream = torch.cuda.current_stream()
     table = {"redc32_2p20": extra_redc32, "rns64_batched": extra_rns64, "cios": extra_cios,
              "limb_variants": extra_limb_variants, "sweep_r16": extra_sweep, "ntt": extra_ntt,
              "dot_lazy": extra_dot, "rns_convert": extra_rns}
     out = {}
     for name in names:
+        if name == "serving":
+            out[name] = extra_serving(mg, 10000, stream, peak, out.get("sweep_r16"))
+            continue
         fn = table[name]
         out[name] = fn(mg, stream, peak) if fn.__code__.co_argcount == 3 else fn(mg, stream)
     return {"extras": out}

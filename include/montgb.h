@@ -504,9 +504,9 @@ int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t
  * Every call on a device shares the one array and it keeps the previous
  * call's contents (the call clears its counters itself), so calls whose GPU
  * work overlaps in time -- on different streams or host threads -- race and
- * must be serialised by the caller.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current
- * and caches it; make that first call before any stream capture begins.
+ * must be serialised by the caller.  Each call looks up the array's device
+ * address in the current device's context (cudaGetSymbolAddress, which
+ * allocates nothing) and synchronises `stream` before it returns.
  */
 #define MONT_SWEEP_NOALLOC_MAX_MODULI 8192
 #define MONT_SWEEP_NOALLOC_MAX_CEX    4096
@@ -522,19 +522,30 @@ int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint32_t N_lo, 
  * verify sweeps (Section 3's check), batched continuously on one GPU.
  *
  * The server owns a device arena of mem_budget_bytes and `slots` worker
- * threads, each with its own CUDA stream.  Jobs wait in one FIFO queue; the
- * job at its head is admitted by the next idle worker as soon as its device
- * buffers fit in the arena (3 * n * element bytes for a modmul job; a
- * sweep reserves an estimate of its scratch), so requests arriving while
- * others run start as soon as a slot and memory free up, and up to `slots`
- * jobs overlap on the device.  A modmul job copies a and b from host memory
- * into the arena, runs mont_mul and copies the products back into `out`;
- * pinned host buffers let the copies run asynchronously.  Contexts stay
- * with the caller (resident across jobs).  A modmul job's wait for the
- * device is bounded by job_timeout_ms (<= 0: 60 s): a job that exceeds it
- * completes with MONT_ETIMEOUT and its arena region is retired (never
- * reused).  A sweep job runs mont_verify_sweep, which synchronises its
- * stream itself.
+ * threads, each with a high-priority CUDA stream (modmul jobs) and a
+ * low-priority one (sweep jobs).  Jobs wait in two FIFO queues, modmul and
+ * sweep; the job at a queue's head is admitted by the next idle worker that
+ * serves that queue as soon as its device memory fits in the arena
+ * (3 * n * element bytes for a modmul job; the table, counters and example
+ * buffer for a sweep), so requests arriving while others run start as soon
+ * as a slot and memory free up, and up to `slots` jobs overlap on the device.
+ * Workers 0 .. max(1, slots/4) - 1 take sweeps first and modmul jobs
+ * otherwise; the rest take modmul jobs only, so a modmul job never queues
+ * behind a sweep.  A modmul job copies a and b from host memory into the
+ * arena, runs mont_mul and copies the products back into `out`; pinned host
+ * buffers let the copies run asynchronously.  A sweep job runs the sweep of
+ * mont_verify_sweep in launches of about 2^31 checks each, so that modmul
+ * jobs' kernels run between them.  Contexts stay with the caller (resident
+ * across jobs).
+ *
+ * Every wait for the device is bounded by the job's timeout (its own
+ * timeout_ms, else the server's job_timeout_ms; <= 0: 60 s).  A job past its
+ * timeout completes with MONT_ETIMEOUT while its device work may still run:
+ * until that work ends, its arena region stays reserved and -- for a modmul
+ * job -- the device may still read a and b and write out.  The caller must
+ * keep a, b, out and ctx valid until mont_server_job_busy reports 0 for the
+ * job (or until mont_server_destroy has returned MONT_OK).  A timed-out sweep
+ * writes none of its result buffers.
  */
 #define MONT_JOB_MODMUL 0
 #define MONT_JOB_SWEEP  1
@@ -542,14 +553,15 @@ int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint32_t N_lo, 
 typedef struct mont_job {
   int kind;                    /* MONT_JOB_MODMUL or MONT_JOB_SWEEP                     */
   /* MODMUL: out[i] = reduce(a[i] b[i]) for ctx; a, b, out HOST pointers of n elements;
-   * ctx and the buffers must stay valid until the job completes.                         */
+   * ctx and the buffers must stay valid until the job completes (and, after
+   * MONT_ETIMEOUT, until mont_server_job_busy reports 0).                                */
   mont_ctx_t ctx;
   const void* a;
   const void* b;
   void* out;
   size_t n;
   /* SWEEP: the arguments of mont_verify_sweep; the result buffers must stay valid
-   * until the job completes (claimed is copied at submission).                          */
+   * until the job completes (claimed is copied, and the request checked, at submission). */
   int variant, log2R, alpha;
   uint32_t N_lo, N_hi;
   const mont_bounds* claimed;
@@ -559,6 +571,7 @@ typedef struct mont_job {
   mont_cex* cex;
   size_t cex_cap;
   size_t* n_cex_total;
+  int timeout_ms;              /* this job's bound on device waits; <= 0: the server's  */
 } mont_job;
 
 typedef struct mont_job_result {
@@ -576,16 +589,25 @@ typedef struct mont_server* mont_server_t;
 int mont_server_create(mont_server_t* out, size_t mem_budget_bytes, int slots,
                        int job_timeout_ms);
 /* Queue a job (copied; never blocks on the device) and return its id.
- * MONT_ENOMEM if the job alone exceeds the budget; MONT_EINVAL on bad fields. */
+ * MONT_ENOMEM if the job alone exceeds the budget; MONT_EINVAL on bad fields
+ * (for a sweep, any request mont_verify_sweep would refuse).  A job that can
+ * never be admitted -- nothing running, and the memory held by timed-out jobs
+ * not given back within its timeout -- completes with MONT_ENOMEM. */
 int mont_server_submit(mont_server_t server, const mont_job* job, uint64_t* id);
 /* Wait for job `id` (timeout_ms < 0: no limit) and retrieve its result; the
  * id is then forgotten.  MONT_ETIMEOUT if it is not done in time (it can be
  * waited for again); MONT_EINVAL for an unknown or already retrieved id. */
 int mont_server_wait(mont_server_t server, uint64_t id, int timeout_ms, mont_job_result* res);
+/* *busy = 1 while job `id` timed out and its device work may still use its
+ * buffers (see above), else 0; valid before and after mont_server_wait. */
+int mont_server_job_busy(mont_server_t server, uint64_t id, int* busy);
 /* Snapshot: jobs queued, jobs running, free arena bytes, server clock. */
 int mont_server_query(mont_server_t server, size_t* queued, size_t* running,
                       size_t* arena_free, double* now_s);
-/* Finish every queued job, stop the workers and free the server. */
+/* Finish every queued job, stop the workers, wait (per stream, at most twice
+ * the job timeout) for the device work of timed-out jobs and free the server.
+ * MONT_ETIMEOUT if that work did not end: the arena is then left allocated
+ * (the device may still write it) and the buffers of those jobs stay in use. */
 int mont_server_destroy(mont_server_t server);
 
 /* ------------------------------------------------------------ autotuner */
@@ -596,7 +618,9 @@ int mont_server_destroy(mont_server_t server);
  * only, never results.
  */
 typedef struct mont_launch_shape {
-  int threads;        /* threads per block: 64..512 (word kernels), 128 or 256 (others) */
+  int threads;        /* threads per block: 64..512 (word kernels), 64, 128 or 256
+                         (multi-limb), 128 or 256 (batched); multi-limb REDC reports 0
+                         when untuned: the block size then follows the element count */
   int unroll;         /* 256-bit vectors in flight per thread per operand: 1, 2 or 4      */
   int vec_bytes;      /* word kernels: 32, 16 or 0 (scalar loads)                         */
   int blocks_per_sm;  /* resident blocks per SM the grid is sized for; 0 = occupancy max   */

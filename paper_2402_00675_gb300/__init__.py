@@ -107,7 +107,7 @@ class MontJob(ctypes.Structure):
                 ("per_N_counts", ctypes.POINTER(ctypes.c_uint64)),
                 ("per_N_checked", ctypes.POINTER(ctypes.c_uint64)),
                 ("cex", ctypes.POINTER(MontCex)), ("cex_cap", ctypes.c_size_t),
-                ("n_cex_total", ctypes.POINTER(ctypes.c_size_t))]
+                ("n_cex_total", ctypes.POINTER(ctypes.c_size_t)), ("timeout_ms", ctypes.c_int)]
 
 
 class MontJobResult(ctypes.Structure):
@@ -183,6 +183,7 @@ def _declare(L):
         "mont_server_create": (_int, [_c.POINTER(_vp), _sz, _int, _int]),
         "mont_server_submit": (_int, [_vp, _c.POINTER(MontJob), _c.POINTER(_c.c_uint64)]),
         "mont_server_wait": (_int, [_vp, _c.c_uint64, _int, _c.POINTER(MontJobResult)]),
+        "mont_server_job_busy": (_int, [_vp, _c.c_uint64, _c.POINTER(_int)]),
         "mont_server_query": (_int, [_vp, _c.POINTER(_sz), _c.POINTER(_sz), _c.POINTER(_sz),
                                      _c.POINTER(_c.c_double)]),
         "mont_server_destroy": (_int, [_vp]),
@@ -525,7 +526,11 @@ def _host_ptr(x):
 
 
 class Server:
-    """A mont_server_t: continuous batching of modmul and sweep jobs."""
+    """A mont_server_t: continuous batching of modmul and sweep jobs.
+
+    The host buffers of a job are kept referenced until the job is retrieved
+    by wait(), and, for a job that timed out, until the server reports that
+    its device work no longer uses them (job_busy)."""
 
     def __init__(self, mem_budget_bytes: int, slots: int = 4, job_timeout_ms: int = 60000):
         h = ctypes.c_void_p()
@@ -533,13 +538,15 @@ class Server:
                                         job_timeout_ms), "mont_server_create")
         self.handle = h.value
         self._keep = {}
+        self._busy = {}   # timed-out jobs whose buffers the device may still use
 
-    def submit_modmul(self, ctx: Ctx, a, b, out, n: int | None = None) -> int:
+    def submit_modmul(self, ctx: Ctx, a, b, out, n: int | None = None,
+                      timeout_ms: int = 0) -> int:
         """Queue out = a b R^{-1} (host buffers) and return the job id."""
         if n is None:
             n = _nbytes(out) // ctx.elem_bytes if hasattr(out, "numel") else out.nbytes // ctx.elem_bytes
         job = MontJob(kind=MONT_JOB_MODMUL, ctx=ctx.handle, a=_host_ptr(a), b=_host_ptr(b),
-                      out=_host_ptr(out), n=n)
+                      out=_host_ptr(out), n=n, timeout_ms=timeout_ms)
         jid = ctypes.c_uint64()
         _check(lib().mont_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)),
                "mont_server_submit")
@@ -547,7 +554,7 @@ class Server:
         return jid.value
 
     def submit_sweep(self, variant, log2R, alpha, N_lo, N_hi, claimed=None, flags=0,
-                     cex_cap=1024) -> int:
+                     cex_cap=1024, timeout_ms: int = 0) -> int:
         first = N_lo if N_lo % 2 else N_lo + 1
         moduli = list(range(first, N_hi + 1, 2))
         n = max(len(moduli), 1)
@@ -558,7 +565,7 @@ class Server:
         job = MontJob(kind=MONT_JOB_SWEEP, variant=variant, log2R=log2R, alpha=alpha, N_lo=N_lo,
                       N_hi=N_hi, claimed=ctypes.pointer(claimed) if claimed is not None else None,
                       flags=flags, per_N_counts=counts, per_N_checked=checked, cex=cex,
-                      cex_cap=cex_cap, n_cex_total=ctypes.pointer(total))
+                      cex_cap=cex_cap, n_cex_total=ctypes.pointer(total), timeout_ms=timeout_ms)
         jid = ctypes.c_uint64()
         _check(lib().mont_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)),
                "mont_server_submit")
@@ -573,7 +580,9 @@ class Server:
         out = {"status": res.status, "t_submit": res.t_submit, "t_admit": res.t_admit,
                "t_done": res.t_done}
         keep = self._keep.pop(jid, None)
-        if keep is not None and len(keep) == 6:
+        if res.status == MONT_ETIMEOUT and keep is not None:
+            self._busy[jid] = keep
+        elif keep is not None and len(keep) == 6 and res.status == MONT_OK:
             moduli, counts, checked, cex, total, cap = keep
             nrec = min(total.value, cap)
             out["sweep"] = SweepResult(
@@ -583,17 +592,32 @@ class Server:
                 total.value, total.value > cap)
         return out
 
+    def job_busy(self, jid: int) -> bool:
+        """True while a timed-out job's device work may still use its buffers."""
+        b = ctypes.c_int()
+        _check(lib().mont_server_job_busy(self.handle, jid, ctypes.byref(b)),
+               "mont_server_job_busy")
+        if not b.value:
+            self._busy.pop(jid, None)
+        return bool(b.value)
+
     def query(self) -> dict:
         q, r, f, t = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_double()
         _check(lib().mont_server_query(self.handle, ctypes.byref(q), ctypes.byref(r),
                                        ctypes.byref(f), ctypes.byref(t)), "mont_server_query")
         return {"queued": q.value, "running": r.value, "arena_free": f.value, "now": t.value}
 
-    def close(self):
+    def close(self) -> int:
+        """Destroy the server; returns its status (MONT_ETIMEOUT: the device work
+        of timed-out jobs did not end, and their buffers stay referenced)."""
+        st = MONT_OK
         if self.handle:
-            lib().mont_server_destroy(self.handle)
+            st = lib().mont_server_destroy(self.handle)
             self.handle = None
             self._keep.clear()
+            if st == MONT_OK:
+                self._busy.clear()
+        return st
 
     def __del__(self):
         try:

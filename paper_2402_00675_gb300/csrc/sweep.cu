@@ -20,29 +20,10 @@
 #include <vector>
 
 #include "internal.h"
+#include "sweep.h"
 
 namespace montgb {
 namespace {
-
-struct SweepN {
-  int32_t N;
-  uint32_t nprime;   // -N^{-1} mod R
-  uint32_t ninv;     // N^{-1} mod R (two's complement reading gives N^{-1} mods R)
-  uint32_t step;     // s R^{-1} mod N
-  int64_t t_lo;      // first T of this modulus
-  int64_t t_hi;      // last T
-  int32_t r_lo;      // claimed range (inclusive)
-  int32_t r_hi;
-  uint64_t item0;    // index of this modulus's first chunk
-};
-
-struct SweepParams {
-  int log2R;
-  int n;            // log2R / 2 (Plantard family)
-  int alpha;
-  uint32_t chunk;   // T per chunk
-  int range_kind;   // RangeKind of the claimed range
-};
 
 // NONNEG: every T of the chunk is >= 0 (REDC's own domain), so REDC's sum
 // T + mN is formed in one unsigned word without testing T's sign.
@@ -118,7 +99,7 @@ __device__ __forceinline__ bool exact_bad(int32_t r, uint32_t c, const SweepN& e
 
 __device__ __forceinline__ uint32_t add_mod(uint32_t c, uint32_t s, uint32_t N) {
   const uint32_t x = c + s;            // c, s < N < 2^15
-  return x >= N ? x - N : x;
+  return min(x, x - N);                // x - N wraps above x when x < N
 }
 
 // c + s for a centred c in [-(N-1)/2, (N-1)/2] and 0 <= s < N, kept centred.
@@ -209,17 +190,115 @@ __device__ __forceinline__ uint32_t check_chunk(int64_t T0, uint32_t cnt, const 
   return local;
 }
 
+// The low word of a b + c, written as PTX so that products of the loop index
+// stay multiply-adds instead of becoming induction additions.  With b = 1
+// held in a register (a kernel parameter the compiler cannot see through) it
+// is an addition issued to the multiply-add pipe, which the sweep otherwise
+// leaves half idle while the ALU pipe runs the compares and minima.
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// The same chunk as check_chunk for REDC on non-negative T and for Algorithm
+// 1, with the work spread over both integer pipes.  T = T0 + j + i for chain
+// j at loop offset i.
+//  REDC:   m = (T N') mod R as the low log2R bits of i N' + T_j N' (one
+//          multiply-add), t = (T + mN) >> log2R, r = min(t, t - N) (unsigned:
+//          t - N wraps above t when t < N, so this is "if t >= N: t - N").
+//  Alg. 1: u = T (N^{-1} << sh) mod 2^32 (sh = 32 - log2R) read as a signed
+//          word is m0 << sh, m0 = T N^{-1} mods R (the sign extension of the
+//          low log2R bits), so floor(m0 N / R) is the signed high word of u N;
+//          a1 = T >> log2R; r = a1 - floor(m0 N / R).
+// The reference chains step with two multiply-adds and one minimum.
+template <int V, int RK>
+__device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, const SweepN& e,
+                                                     const SweepParams& p, uint32_t c0,
+                                                     uint32_t c1, uint32_t c2, uint32_t c3,
+                                                     uint32_t s1, uint32_t s4,
+                                                     mont_cex* __restrict__ cex,
+                                                     unsigned long long* __restrict__ cex_n,
+                                                     unsigned long long cap, bool& full) {
+  constexpr bool kUnsignedTarget = (V == MONT_REDC);
+  const uint32_t N = static_cast<uint32_t>(e.N);
+  const uint32_t one = p.one;
+  const uint32_t negN = 0u - N;
+  const uint32_t s4m = s4 - N;                   // s4 - N mod 2^32
+  const int L = p.log2R;
+  const uint32_t mask = (1u << L) - 1u;
+  const uint32_t k = V == MONT_REDC ? e.nprime : e.ninv << (32 - L);
+  const uint32_t T0w = static_cast<uint32_t>(static_cast<int32_t>(T0));
+  uint32_t Tb[4], kb[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    Tb[j] = T0w + static_cast<uint32_t>(j);
+    kb[j] = Tb[j] * k;
+  }
+  uint32_t c[4] = {c0, c1, c2, c3};
+  uint32_t local = 0;
+  uint32_t i = 0;
+  for (; i + 4 <= cnt; i += 4) {
+    int32_t r[4];
+    bool g[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t T = mad_lo(i, one, Tb[j]);
+      const uint32_t u = mad_lo(i, k, kb[j]);            // T k mod 2^32
+      if constexpr (V == MONT_REDC) {
+        const uint32_t t = mad_lo(u & mask, N, T) >> L;  // (T + mN) / R, below 2^32
+        r[j] = static_cast<int32_t>(min(t, mad_lo(t, one, negN)));
+      } else {
+        r[j] = (static_cast<int32_t>(T) >> L) -
+               __mulhi(static_cast<int32_t>(u), static_cast<int32_t>(N));
+      }
+      g[j] = fast_good<RK>(r[j], c[j], e);
+    }
+    if (!(g[0] && g[1] && g[2] && g[3])) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!g[j] && exact_bad(r[j], c[j], e)) {
+          ++local;
+          if (!full)
+            full = record<kUnsignedTarget>(static_cast<int32_t>(T0w + i + static_cast<uint32_t>(j)),
+                                           r[j], c[j], N, cex, cex_n, cap);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if constexpr (RK == kCentred) {
+        c[j] = step_ref<RK>(c[j], s4, N);
+      } else {
+        c[j] = min(mad_lo(c[j], one, s4), mad_lo(c[j], one, s4m));
+      }
+    }
+  }
+  for (; i < cnt; ++i) {
+    const int32_t T = static_cast<int32_t>(T0w + i);
+    const int32_t r = candidate<V, true>(T, e, p);
+    if (!fast_good<RK>(r, c[0], e) && exact_bad(r, c[0], e)) {
+      ++local;
+      if (!full) full = record<kUnsignedTarget>(T, r, c[0], N, cex, cex_n, cap);
+    }
+    c[0] = step_ref<RK>(c[0], s1, N);
+  }
+  return local;
+}
+
+// Chunks item_lo .. item_hi - 1 of the sweep, grid-stride.
 template <int V, int RK>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ tab, int n_tab,
-                                                    uint64_t n_items, SweepParams p,
+                                                    uint64_t item_lo, uint64_t item_hi,
+                                                    SweepParams p,
                                                     unsigned long long* __restrict__ counts,
                                                     mont_cex* __restrict__ cex,
                                                     unsigned long long* __restrict__ cex_n,
                                                     unsigned long long cap) {
   const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   bool full = false;  // the example buffer was seen full: stop touching it
-  for (uint64_t item = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; item < n_items;
-       item += nthreads) {
+  for (uint64_t item = item_lo + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+       item < item_hi; item += nthreads) {
     int lo = 0, hi = n_tab - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -244,10 +323,16 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepN* __restrict__ t
       c2 = c2 > h ? c2 - N : c2;
       c3 = c3 > h ? c3 - N : c3;
     }
-    const uint32_t local =
-        (V == MONT_REDC && T0 >= 0)
-            ? check_chunk<V, RK, true>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full)
-            : check_chunk<V, RK, false>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full);
+    uint32_t local;
+    if constexpr (V == MONT_SIGNED) {
+      local = check_chunk_fast<V, RK>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full);
+    } else if constexpr (V == MONT_REDC) {
+      local = T0 >= 0
+                  ? check_chunk_fast<V, RK>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full)
+                  : check_chunk<V, RK, false>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full);
+    } else {
+      local = check_chunk<V, RK, false>(T0, cnt, e, p, c0, c1, c2, c3, s1, s4, cex, cex_n, cap, full);
+    }
     if (local) atomicAdd(counts + lo, static_cast<unsigned long long>(local));
   }
 }
@@ -309,15 +394,17 @@ void default_range(int variant, int64_t N, int64_t* lo, int64_t* hi) {
 }
 
 template <int V, int RK>
-cudaError_t launch_sweep_rk(const SweepN* tab, int n_tab, uint64_t n_items, const SweepParams& p,
-                            unsigned long long* counts, mont_cex* cex, unsigned long long* cex_n,
-                            unsigned long long cap, cudaStream_t s) {
+cudaError_t launch_sweep_rk(const SweepN* tab, int n_tab, uint64_t item_lo, uint64_t item_hi,
+                            const SweepParams& p, unsigned long long* counts, mont_cex* cex,
+                            unsigned long long* cex_n, unsigned long long cap, cudaStream_t s) {
+  if (item_hi <= item_lo) return cudaSuccess;
   const int threads = 256;
   const int per_sm = resident_blocks(reinterpret_cast<const void*>(sweep_kernel<V, RK>), threads);
   const uint64_t cap_blocks = static_cast<uint64_t>(device_sm_count()) * per_sm;
-  const uint64_t want = (n_items + threads - 1) / threads;
+  const uint64_t want = (item_hi - item_lo + threads - 1) / threads;
   const unsigned grid = static_cast<unsigned>(want < cap_blocks ? want : cap_blocks);
-  sweep_kernel<V, RK><<<grid, threads, 0, s>>>(tab, n_tab, n_items, p, counts, cex, cex_n, cap);
+  sweep_kernel<V, RK><<<grid, threads, 0, s>>>(tab, n_tab, item_lo, item_hi, p, counts, cex, cex_n,
+                                               cap);
   return cudaGetLastError();
 }
 
@@ -336,21 +423,223 @@ int range_kind(int variant, int range_rule) {
 }
 
 template <int V>
-cudaError_t launch_sweep(const SweepN* tab, int n_tab, uint64_t n_items, const SweepParams& p,
-                         unsigned long long* counts, mont_cex* cex, unsigned long long* cex_n,
-                         unsigned long long cap, cudaStream_t s) {
+cudaError_t launch_sweep_v(const SweepN* tab, int n_tab, uint64_t lo, uint64_t hi,
+                           const SweepParams& p, unsigned long long* counts, mont_cex* cex,
+                           unsigned long long* cex_n, unsigned long long cap, cudaStream_t s) {
   switch (p.range_kind) {
-    case kUnsigned: return launch_sweep_rk<V, kUnsigned>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
-    case kCentred: return launch_sweep_rk<V, kCentred>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
-    case kWide: return launch_sweep_rk<V, kWide>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
-    default: return launch_sweep_rk<V, kGeneric>(tab, n_tab, n_items, p, counts, cex, cex_n, cap, s);
+    case kUnsigned: return launch_sweep_rk<V, kUnsigned>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    case kCentred: return launch_sweep_rk<V, kCentred>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    case kWide: return launch_sweep_rk<V, kWide>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    default: return launch_sweep_rk<V, kGeneric>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
   }
+}
+
+// Chunks [lo, hi) of a sweep whose table, counters and example buffer are in
+// device memory.
+cudaError_t launch_sweep(int variant, const SweepN* tab, int n_tab, uint64_t lo, uint64_t hi,
+                         const SweepParams& p, unsigned long long* counts, mont_cex* cex,
+                         unsigned long long* cex_n, unsigned long long cap, cudaStream_t s) {
+  switch (variant) {
+    case MONT_REDC: return launch_sweep_v<MONT_REDC>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    case MONT_SIGNED: return launch_sweep_v<MONT_SIGNED>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    case MONT_PLANTARD: return launch_sweep_v<MONT_PLANTARD>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    case MONT_SIGNED_PLANTARD: return launch_sweep_v<MONT_SIGNED_PLANTARD>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+    default: return launch_sweep_v<MONT_SIGNED_PLANTARD2>(tab, n_tab, lo, hi, p, counts, cex, cex_n, cap, s);
+  }
+}
+
+// Where the parts of a sweep's scratch sit, from its 256-byte aligned start.
+struct ScratchLayout {
+  size_t counts, cex_n, cex, total;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+ScratchLayout scratch_layout(size_t n_tab, size_t cex_cap) {
+  ScratchLayout l;
+  l.counts = align256(n_tab * sizeof(SweepN));
+  l.cex_n = l.counts + align256(n_tab * sizeof(unsigned long long));
+  l.cex = l.cex_n + 256;
+  l.total = l.cex + cex_cap * sizeof(mont_cex);
+  return l;
+}
+
+// The checked domain and claimed range of modulus N under the call's rules.
+// Returns false when N is skipped (too small, or outside the variant's
+// condition unless out-of-spec moduli are asked for).
+bool resolve_rules(int variant, int log2R, int alpha, int64_t N, int flags, const mont_bounds& rules,
+                   int64_t* tlo, int64_t* thi, int64_t* rlo, int64_t* rhi) {
+  if (N < 3) return false;
+  if (!(flags & MONT_SWEEP_INCLUDE_OUT_OF_SPEC) && !precondition(variant, N, log2R, alpha)) return false;
+  const int64_t R = int64_t{1} << log2R;
+  if (rules.domain_rule == MONT_DOMAIN_DEFAULT) {
+    default_domain(variant, N, log2R, alpha, tlo, thi);
+  } else if (rules.domain_rule == MONT_DOMAIN_REDC) {
+    *tlo = 0;
+    *thi = R * N - 1;
+  } else {
+    *tlo = rules.t_lo;
+    *thi = rules.t_hi;
+  }
+  switch (rules.range_rule) {
+    case MONT_RANGE_DEFAULT: default_range(variant, N, rlo, rhi); break;
+    case MONT_RANGE_UNSIGNED: *rlo = 0; *rhi = N - 1; break;
+    case MONT_RANGE_WIDE: *rlo = -(N - 1); *rhi = N - 1; break;
+    case MONT_RANGE_CENTRED: *rlo = -((N - 1) / 2); *rhi = (N - 1) / 2; break;
+    default: *rlo = rules.r_lo; *rhi = rules.r_hi; break;
+  }
+  return true;
+}
+
+// The constants of a table entry for N (its T interval and range set by the caller).
+void fill_constants(int variant, int log2R, int64_t N, SweepN* e) {
+  const uint32_t mask = (1u << log2R) - 1u;
+  const int64_t R = int64_t{1} << log2R;
+  e->N = static_cast<int32_t>(N);
+  e->ninv = inv_pow2_u32(static_cast<uint32_t>(N), mask);
+  e->nprime = (0u - e->ninv) & mask;
+  const int64_t rinv = inv_mod(R % N, N);
+  e->step = static_cast<uint32_t>(variant >= MONT_PLANTARD ? (N - rinv) % N : rinv);
+}
+
+// The argument checks every sweep entry point shares.
+int check_args(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t N_hi,
+               const mont_bounds& rules) {
+  if (variant < MONT_REDC || variant > MONT_SIGNED_PLANTARD2) return MONT_EINVAL;
+  if (log2R < 2 || log2R > MONT_SWEEP_MAX_LOG2R) return MONT_EINVAL;
+  if (variant >= MONT_PLANTARD && (log2R % 2)) return MONT_EINVAL;
+  if (variant == MONT_SIGNED_PLANTARD2 && (alpha < 0 || alpha > 14)) return MONT_EINVAL;
+  if (N_lo > N_hi || N_hi > MONT_SWEEP_MAX_N || N_hi < 3) return MONT_EINVAL;
+  if (rules.domain_rule < MONT_DOMAIN_DEFAULT || rules.domain_rule > MONT_DOMAIN_EXPLICIT) return MONT_EINVAL;
+  if (rules.range_rule < MONT_RANGE_DEFAULT || rules.range_rule > MONT_RANGE_EXPLICIT) return MONT_EINVAL;
+  return MONT_OK;
+}
+
+// Chunk size: a power of two in [32, 4096] giving >= 8 chunks per resident
+// thread of a full-occupancy grid.
+uint64_t chunk_for(uint64_t total_T) {
+  const uint64_t resident = static_cast<uint64_t>(device_sm_count()) * 2048u;
+  uint64_t chunk = 4096;
+  while (chunk > 32 && total_T / chunk < 8 * resident) chunk >>= 1;
+  return chunk;
 }
 
 }  // namespace
 
-// Threads of one full-occupancy grid, for sizing chunks.
-static uint64_t resident_threads() { return static_cast<uint64_t>(device_sm_count()) * 2048u; }
+int sweep_plan(int variant, int log2R, int alpha, uint32_t N_lo, uint32_t N_hi,
+               const mont_bounds* claimed, int flags, size_t cex_cap, uint64_t* per_N_counts,
+               uint64_t* per_N_checked, SweepPlan* plan) {
+  mont_bounds rules{MONT_DOMAIN_DEFAULT, MONT_RANGE_DEFAULT, 0, 0, 0, 0};
+  if (claimed) rules = *claimed;
+  const int st = check_args(variant, log2R, alpha, N_lo, N_hi, rules);
+  if (st != MONT_OK) return st;
+  if (!per_N_counts) return MONT_EINVAL;
+  const uint32_t first = (N_lo % 2) ? N_lo : N_lo + 1;
+  plan->variant = variant;
+  plan->cex_cap = cex_cap;
+  plan->n_odd = first > N_hi ? 0 : (N_hi - first) / 2 + 1;
+  plan->tab.clear();
+  plan->tab_index.clear();
+  plan->total_T = 0;
+  for (size_t i = 0; i < plan->n_odd; ++i) {
+    per_N_counts[i] = 0;
+    if (per_N_checked) per_N_checked[i] = 0;
+  }
+  for (size_t i = 0; i < plan->n_odd; ++i) {
+    const int64_t N = first + 2 * static_cast<int64_t>(i);
+    int64_t tlo, thi, rlo, rhi;
+    if (!resolve_rules(variant, log2R, alpha, N, flags, rules, &tlo, &thi, &rlo, &rhi)) continue;
+    if (tlo > thi) continue;  // empty domain: nothing checked
+    if (tlo < INT32_MIN || thi > INT32_MAX || rlo < INT32_MIN || rhi > INT32_MAX || rlo > rhi)
+      return MONT_EINVAL;
+    SweepN e{};
+    fill_constants(variant, log2R, N, &e);
+    e.t_lo = tlo;
+    e.t_hi = thi;
+    e.r_lo = static_cast<int32_t>(rlo);
+    e.r_hi = static_cast<int32_t>(rhi);
+    plan->tab.push_back(e);
+    plan->tab_index.push_back(i);
+    plan->total_T += static_cast<uint64_t>(thi - tlo + 1);
+    if (per_N_checked) per_N_checked[i] = static_cast<uint64_t>(thi - tlo + 1);
+  }
+  const uint64_t chunk = plan->tab.empty() ? 32 : chunk_for(plan->total_T);
+  plan->items = 0;
+  for (auto& e : plan->tab) {
+    e.item0 = plan->items;
+    plan->items += (static_cast<uint64_t>(e.t_hi - e.t_lo) + chunk) / chunk;
+  }
+  plan->p = SweepParams{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk),
+                        range_kind(variant, rules.range_rule), 1u};
+  return MONT_OK;
+}
+
+size_t sweep_scratch_bytes(size_t n_tab, size_t cex_cap) {
+  return scratch_layout(n_tab, cex_cap).total;
+}
+
+cudaError_t sweep_upload(const SweepPlan& plan, void* scratch, cudaStream_t s) {
+  const ScratchLayout l = scratch_layout(plan.tab.size(), plan.cex_cap);
+  char* base = static_cast<char*>(scratch);
+  cudaError_t e = cudaMemcpyAsync(base, plan.tab.data(), plan.tab.size() * sizeof(SweepN),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(base + l.counts, 0, plan.tab.size() * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + l.cex_n, 0, sizeof(unsigned long long), s);
+  return e;
+}
+
+cudaError_t sweep_launch(const SweepPlan& plan, void* scratch, uint64_t item_lo, uint64_t item_hi,
+                         cudaStream_t s) {
+  if (plan.tab.empty()) return cudaSuccess;
+  const ScratchLayout l = scratch_layout(plan.tab.size(), plan.cex_cap);
+  char* base = static_cast<char*>(scratch);
+  if (item_hi > plan.items) item_hi = plan.items;
+  return launch_sweep(plan.variant, reinterpret_cast<const SweepN*>(base),
+                      static_cast<int>(plan.tab.size()), item_lo, item_hi, plan.p,
+                      reinterpret_cast<unsigned long long*>(base + l.counts),
+                      reinterpret_cast<mont_cex*>(base + l.cex),
+                      reinterpret_cast<unsigned long long*>(base + l.cex_n), plan.cex_cap, s);
+}
+
+uint64_t sweep_items_for_checks(const SweepPlan& plan, uint64_t checks) {
+  const uint64_t per = checks / (plan.p.chunk ? plan.p.chunk : 1);
+  return per ? per : 1;
+}
+
+int sweep_collect(const SweepPlan& plan, void* scratch, cudaStream_t s, uint64_t* per_N_counts,
+                  mont_cex* cex, size_t* n_cex_total) {
+  *n_cex_total = 0;
+  const size_t n_tab = plan.tab.size();
+  if (n_tab == 0) return MONT_OK;
+  const ScratchLayout l = scratch_layout(n_tab, plan.cex_cap);
+  char* base = static_cast<char*>(scratch);
+  std::vector<unsigned long long> h_counts(n_tab);
+  unsigned long long h_cex_n = 0;
+  cudaError_t err = cudaMemcpyAsync(h_counts.data(), base + l.counts,
+                                    n_tab * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&h_cex_n, base + l.cex_n, sizeof(h_cex_n), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  size_t n_rec = 0;
+  if (err == cudaSuccess) {
+    n_rec = static_cast<size_t>(h_cex_n < plan.cex_cap ? h_cex_n : plan.cex_cap);
+    if (n_rec)
+      err = cudaMemcpyAsync(cex, base + l.cex, n_rec * sizeof(mont_cex), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  }
+  if (err != cudaSuccess) return cuda_status(err);
+  uint64_t total = 0;
+  for (size_t j = 0; j < n_tab; ++j) {
+    per_N_counts[plan.tab_index[j]] = h_counts[j];
+    total += h_counts[j];
+  }
+  std::sort(cex, cex + n_rec, [](const mont_cex& a, const mont_cex& b) {
+    return a.N != b.N ? a.N < b.N : a.T < b.T;
+  });
+  *n_cex_total = static_cast<size_t>(total);
+  return total > plan.cex_cap ? MONT_EOVERFLOW : MONT_OK;
+}
 
 }  // namespace montgb
 
@@ -360,183 +649,69 @@ extern "C" int mont_verify_sweep(int variant, int log2R, int alpha, uint32_t N_l
                                  const mont_bounds* claimed, int flags, uint64_t* per_N_counts,
                                  uint64_t* per_N_checked, mont_cex* cex, size_t cex_cap,
                                  size_t* n_cex_total, void* stream) {
-  if (variant < MONT_REDC || variant > MONT_SIGNED_PLANTARD2) return MONT_EINVAL;
-  if (log2R < 2 || log2R > MONT_SWEEP_MAX_LOG2R) return MONT_EINVAL;
-  if (variant >= MONT_PLANTARD && (log2R % 2)) return MONT_EINVAL;
-  if (variant == MONT_SIGNED_PLANTARD2 && (alpha < 0 || alpha > 14)) return MONT_EINVAL;
-  if (N_lo > N_hi || N_hi > MONT_SWEEP_MAX_N || N_hi < 3) return MONT_EINVAL;
   if (!per_N_counts || !n_cex_total || (cex_cap > 0 && !cex)) return MONT_EINVAL;
-  mont_bounds rules{MONT_DOMAIN_DEFAULT, MONT_RANGE_DEFAULT, 0, 0, 0, 0};
-  if (claimed) rules = *claimed;
-  if (rules.domain_rule < MONT_DOMAIN_DEFAULT || rules.domain_rule > MONT_DOMAIN_EXPLICIT) return MONT_EINVAL;
-  if (rules.range_rule < MONT_RANGE_DEFAULT || rules.range_rule > MONT_RANGE_EXPLICIT) return MONT_EINVAL;
-  const int64_t kMin = INT32_MIN, kMax = INT32_MAX;
-
-  const uint32_t first = (N_lo % 2) ? N_lo : N_lo + 1;
-  const size_t n_odd = first > N_hi ? 0 : (N_hi - first) / 2 + 1;
-  std::vector<SweepN> tab;
-  std::vector<size_t> tab_index;  // position of each table entry among the odd N
-  const uint32_t mask = (1u << log2R) - 1u;
-  const int64_t R = int64_t{1} << log2R;
-  uint64_t total_T = 0;
-  for (size_t i = 0; i < n_odd; ++i) {
-    per_N_counts[i] = 0;
-    if (per_N_checked) per_N_checked[i] = 0;
-  }
-  for (size_t i = 0; i < n_odd; ++i) {
-    const int64_t N = first + 2 * static_cast<int64_t>(i);
-    if (N < 3) continue;
-    if (!(flags & MONT_SWEEP_INCLUDE_OUT_OF_SPEC) && !precondition(variant, N, log2R, alpha)) continue;
-    int64_t tlo, thi, rlo, rhi;
-    if (rules.domain_rule == MONT_DOMAIN_DEFAULT) {
-      default_domain(variant, N, log2R, alpha, &tlo, &thi);
-    } else if (rules.domain_rule == MONT_DOMAIN_REDC) {
-      tlo = 0; thi = R * N - 1;
-    } else {
-      tlo = rules.t_lo; thi = rules.t_hi;
-    }
-    switch (rules.range_rule) {
-      case MONT_RANGE_DEFAULT: default_range(variant, N, &rlo, &rhi); break;
-      case MONT_RANGE_UNSIGNED: rlo = 0; rhi = N - 1; break;
-      case MONT_RANGE_WIDE: rlo = -(N - 1); rhi = N - 1; break;
-      case MONT_RANGE_CENTRED: rlo = -((N - 1) / 2); rhi = (N - 1) / 2; break;
-      default: rlo = rules.r_lo; rhi = rules.r_hi; break;
-    }
-    if (tlo > thi) continue;  // empty domain: nothing checked
-    if (tlo < kMin || thi > kMax || rlo < kMin || rhi > kMax || rlo > rhi) return MONT_EINVAL;
-    SweepN e{};
-    e.N = static_cast<int32_t>(N);
-    e.ninv = inv_pow2_u32(static_cast<uint32_t>(N), mask);
-    e.nprime = (0u - e.ninv) & mask;
-    const int64_t rinv = inv_mod(R % N, N);
-    e.step = static_cast<uint32_t>(variant >= MONT_PLANTARD ? (N - rinv) % N : rinv);
-    e.t_lo = tlo;
-    e.t_hi = thi;
-    e.r_lo = static_cast<int32_t>(rlo);
-    e.r_hi = static_cast<int32_t>(rhi);
-    tab.push_back(e);
-    tab_index.push_back(i);
-    total_T += static_cast<uint64_t>(thi - tlo + 1);
-    if (per_N_checked) per_N_checked[i] = static_cast<uint64_t>(thi - tlo + 1);
-  }
+  SweepPlan plan;
+  const int st = sweep_plan(variant, log2R, alpha, N_lo, N_hi, claimed, flags, cex_cap,
+                            per_N_counts, per_N_checked, &plan);
+  if (st != MONT_OK) return st;
   *n_cex_total = 0;
-  if (tab.empty()) return MONT_OK;
-
-  // Chunk size: a power of two in [32, 4096] giving >= 8 chunks per resident thread.
-  uint64_t chunk = 4096;
-  while (chunk > 32 && total_T / chunk < 8 * resident_threads()) chunk >>= 1;
-  uint64_t items = 0;
-  for (auto& e : tab) {
-    e.item0 = items;
-    items += (static_cast<uint64_t>(e.t_hi - e.t_lo) + chunk) / chunk;
-  }
-  SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk),
-                range_kind(variant, rules.range_rule)};
+  if (plan.tab.empty()) return MONT_OK;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t n_tab = tab.size();
-  const size_t dev_cap = cex_cap;
-  const size_t bytes = n_tab * sizeof(SweepN) + n_tab * sizeof(unsigned long long) +
-                       sizeof(unsigned long long) + dev_cap * sizeof(mont_cex) + 256;
   void* scratch = nullptr;
-  cudaError_t err = cudaMallocAsync(&scratch, bytes, s);
+  cudaError_t err = cudaMallocAsync(&scratch, sweep_scratch_bytes(plan.tab.size(), cex_cap), s);
   if (err != cudaSuccess) {
     cudaGetLastError();
     return err == cudaErrorMemoryAllocation ? MONT_ENOMEM : cuda_status(err);
   }
-  char* base = static_cast<char*>(scratch);
-  SweepN* d_tab = reinterpret_cast<SweepN*>(base);
-  auto* d_counts = reinterpret_cast<unsigned long long*>(base + n_tab * sizeof(SweepN));
-  auto* d_cex_n = d_counts + n_tab;
-  auto* d_cex = reinterpret_cast<mont_cex*>(
-      (reinterpret_cast<uintptr_t>(d_cex_n + 1) + 15) & ~static_cast<uintptr_t>(15));
-  std::vector<unsigned long long> h_counts(n_tab);
-  unsigned long long h_cex_n = 0;
-  int status = MONT_OK;
-
-  err = cudaMemcpyAsync(d_tab, tab.data(), n_tab * sizeof(SweepN), cudaMemcpyHostToDevice, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(d_counts, 0, (n_tab + 1) * sizeof(unsigned long long), s);
-  if (err == cudaSuccess) {
-    switch (variant) {
-      case MONT_REDC: err = launch_sweep<MONT_REDC>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
-      case MONT_SIGNED: err = launch_sweep<MONT_SIGNED>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
-      case MONT_PLANTARD: err = launch_sweep<MONT_PLANTARD>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
-      case MONT_SIGNED_PLANTARD: err = launch_sweep<MONT_SIGNED_PLANTARD>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
-      default: err = launch_sweep<MONT_SIGNED_PLANTARD2>(d_tab, (int)n_tab, items, p, d_counts, d_cex, d_cex_n, dev_cap, s); break;
-    }
+  err = sweep_upload(plan, scratch, s);
+  if (err == cudaSuccess) err = sweep_launch(plan, scratch, 0, plan.items, s);
+  int status = err == cudaSuccess ? sweep_collect(plan, scratch, s, per_N_counts, cex, n_cex_total)
+                                  : cuda_status(err);
+  const cudaError_t ferr = cudaFreeAsync(scratch, s);
+  const cudaError_t serr = cudaStreamSynchronize(s);
+  if (status == MONT_OK || status == MONT_EOVERFLOW) {
+    if (ferr != cudaSuccess) return cuda_status(ferr);
+    if (serr != cudaSuccess) return cuda_status(serr);
   }
-  if (err == cudaSuccess)
-    err = cudaMemcpyAsync(h_counts.data(), d_counts, n_tab * sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, s);
-  if (err == cudaSuccess)
-    err = cudaMemcpyAsync(&h_cex_n, d_cex_n, sizeof(h_cex_n), cudaMemcpyDeviceToHost, s);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  size_t n_rec = 0;
-  if (err == cudaSuccess) {
-    n_rec = static_cast<size_t>(h_cex_n < dev_cap ? h_cex_n : dev_cap);
-    if (n_rec)
-      err = cudaMemcpyAsync(cex, d_cex, n_rec * sizeof(mont_cex), cudaMemcpyDeviceToHost, s);
-  }
-  cudaError_t ferr = cudaFreeAsync(scratch, s);
-  if (err == cudaSuccess) err = ferr;
-  cudaError_t serr = cudaStreamSynchronize(s);
-  if (err == cudaSuccess) err = serr;
-  if (err != cudaSuccess) return cuda_status(err);
-
-  uint64_t total = 0;
-  for (size_t j = 0; j < n_tab; ++j) {
-    per_N_counts[tab_index[j]] = h_counts[j];
-    total += h_counts[j];
-  }
-  std::sort(cex, cex + n_rec, [](const mont_cex& a, const mont_cex& b) {
-    return a.N != b.N ? a.N < b.N : a.T < b.T;
-  });
-  *n_cex_total = static_cast<size_t>(total);
-  if (total > cex_cap) status = MONT_EOVERFLOW;
   return status;
 }
 
 // ---------------------------------------------------------------------------
 // mont_verify_sweep_noalloc: the same sweep for callers that must not
 // allocate.  Its device scratch (moduli table, per-N counters, example
-// buffer) lives in one fixed file-scope array instead of memory allocated per
-// call, and the host side uses only the caller's buffers and a small stack
-// staging array.
+// buffer) lives in one fixed file-scope device array instead of memory
+// allocated per call, and its host side builds the table in one fixed
+// file-scope host array and otherwise uses only the caller's buffers.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr size_t kNoAllocModuli = MONT_SWEEP_NOALLOC_MAX_MODULI;
 constexpr size_t kNoAllocCex = MONT_SWEEP_NOALLOC_MAX_CEX;
-constexpr size_t kNoAllocCountsOff = (kNoAllocModuli * sizeof(SweepN) + 255) / 256 * 256;
-constexpr size_t kNoAllocCexNOff = kNoAllocCountsOff + kNoAllocModuli * sizeof(unsigned long long);
-constexpr size_t kNoAllocCexOff = kNoAllocCexNOff + 256;
-constexpr size_t kNoAllocBytes = kNoAllocCexOff + kNoAllocCex * sizeof(mont_cex);
+constexpr size_t kNoAllocBytes =
+    (kNoAllocModuli * sizeof(SweepN) + 255) / 256 * 256 +
+    (kNoAllocModuli * sizeof(unsigned long long) + 255) / 256 * 256 + 256 +
+    kNoAllocCex * sizeof(mont_cex);
 }  // namespace
 
 // Shared by every call on a device and held until the process exits.  Host
 // code must not take this symbol's address directly (it is a host-side
-// stand-in); it uses the device address cached by noalloc_scratch().
+// stand-in); it uses the device address from noalloc_scratch().
 static __device__ __align__(256) unsigned char g_sweep_noalloc_scratch[kNoAllocBytes];
 
-namespace {
-constexpr int kNoAllocMaxDevices = 256;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// The table of one call, built on the host and uploaded in one copy.  Like the
+// device array it is shared by every call (the call returns only after the
+// copy has consumed it, so one call never sees another's half-built table).
+static SweepN g_noalloc_table[kNoAllocModuli];
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+namespace {
+// Device address of the scratch array in the current device's context,
+// looked up on every call (a lookup allocates nothing, and a cached address
+// would go stale if the context were torn down and created again).
 int noalloc_scratch(char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_noalloc_scratch);
   if (e != cudaSuccess) return cuda_status(e);
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return MONT_EINVAL;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_sweep_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_status(e);
-    g_noalloc_addr[dev] = p;
-  }
-  *out = static_cast<char*>(g_noalloc_addr[dev]);
+  *out = static_cast<char*>(p);
   return MONT_OK;
 }
 
@@ -550,35 +725,12 @@ int noalloc_entry(int variant, int log2R, int alpha, int64_t N, int flags, const
   e->t_lo = 0;
   e->t_hi = -1;
   *checked = 0;
-  if (N < 3) return MONT_OK;
-  if (!(flags & MONT_SWEEP_INCLUDE_OUT_OF_SPEC) && !precondition(variant, N, log2R, alpha))
-    return MONT_OK;
-  const int64_t R = int64_t{1} << log2R;
   int64_t tlo, thi, rlo, rhi;
-  if (rules.domain_rule == MONT_DOMAIN_DEFAULT) {
-    default_domain(variant, N, log2R, alpha, &tlo, &thi);
-  } else if (rules.domain_rule == MONT_DOMAIN_REDC) {
-    tlo = 0;
-    thi = R * N - 1;
-  } else {
-    tlo = rules.t_lo;
-    thi = rules.t_hi;
-  }
-  switch (rules.range_rule) {
-    case MONT_RANGE_DEFAULT: default_range(variant, N, &rlo, &rhi); break;
-    case MONT_RANGE_UNSIGNED: rlo = 0; rhi = N - 1; break;
-    case MONT_RANGE_WIDE: rlo = -(N - 1); rhi = N - 1; break;
-    case MONT_RANGE_CENTRED: rlo = -((N - 1) / 2); rhi = (N - 1) / 2; break;
-    default: rlo = rules.r_lo; rhi = rules.r_hi; break;
-  }
+  if (!resolve_rules(variant, log2R, alpha, N, flags, rules, &tlo, &thi, &rlo, &rhi)) return MONT_OK;
   if (tlo > thi) return MONT_OK;
   if (tlo < INT32_MIN || thi > INT32_MAX || rlo < INT32_MIN || rhi > INT32_MAX || rlo > rhi)
     return MONT_EINVAL;
-  const uint32_t mask = (1u << log2R) - 1u;
-  e->ninv = inv_pow2_u32(static_cast<uint32_t>(N), mask);
-  e->nprime = (0u - e->ninv) & mask;
-  const int64_t rinv = inv_mod(R % N, N);
-  e->step = static_cast<uint32_t>(variant >= MONT_PLANTARD ? (N - rinv) % N : rinv);
+  fill_constants(variant, log2R, N, e);
   e->t_lo = tlo;
   e->t_hi = thi;
   e->r_lo = static_cast<int32_t>(rlo);
@@ -593,16 +745,11 @@ extern "C" int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint
                                          uint64_t* per_N_counts, uint64_t* per_N_checked,
                                          mont_cex* cex, size_t cex_cap, size_t* n_cex_total,
                                          void* stream) {
-  if (variant < MONT_REDC || variant > MONT_SIGNED_PLANTARD2) return MONT_EINVAL;
-  if (log2R < 2 || log2R > MONT_SWEEP_MAX_LOG2R) return MONT_EINVAL;
-  if (variant >= MONT_PLANTARD && (log2R % 2)) return MONT_EINVAL;
-  if (variant == MONT_SIGNED_PLANTARD2 && (alpha < 0 || alpha > 14)) return MONT_EINVAL;
-  if (N_lo > N_hi || N_hi > MONT_SWEEP_MAX_N || N_hi < 3) return MONT_EINVAL;
-  if (!per_N_counts || !n_cex_total || (cex_cap > 0 && !cex)) return MONT_EINVAL;
   mont_bounds rules{MONT_DOMAIN_DEFAULT, MONT_RANGE_DEFAULT, 0, 0, 0, 0};
   if (claimed) rules = *claimed;
-  if (rules.domain_rule < MONT_DOMAIN_DEFAULT || rules.domain_rule > MONT_DOMAIN_EXPLICIT) return MONT_EINVAL;
-  if (rules.range_rule < MONT_RANGE_DEFAULT || rules.range_rule > MONT_RANGE_EXPLICIT) return MONT_EINVAL;
+  const int ast = check_args(variant, log2R, alpha, N_lo, N_hi, rules);
+  if (ast != MONT_OK) return ast;
+  if (!per_N_counts || !n_cex_total || (cex_cap > 0 && !cex)) return MONT_EINVAL;
   const uint32_t first = (N_lo % 2) ? N_lo : N_lo + 1;
   const size_t n_odd = first > N_hi ? 0 : (N_hi - first) / 2 + 1;
   // the fixed scratch bounds the request
@@ -626,48 +773,33 @@ extern "C" int mont_verify_sweep_noalloc(int variant, int log2R, int alpha, uint
   char* scratch = nullptr;
   const int sst = noalloc_scratch(&scratch);
   if (sst != MONT_OK) return sst;
+  const ScratchLayout l = scratch_layout(n_odd, cex_cap);
   SweepN* d_tab = reinterpret_cast<SweepN*>(scratch);
-  auto* d_counts = reinterpret_cast<unsigned long long*>(scratch + kNoAllocCountsOff);
-  auto* d_cex_n = reinterpret_cast<unsigned long long*>(scratch + kNoAllocCexNOff);
-  auto* d_cex = reinterpret_cast<mont_cex*>(scratch + kNoAllocCexOff);
+  auto* d_counts = reinterpret_cast<unsigned long long*>(scratch + l.counts);
+  auto* d_cex_n = reinterpret_cast<unsigned long long*>(scratch + l.cex_n);
+  auto* d_cex = reinterpret_cast<mont_cex*>(scratch + l.cex);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t chunk = chunk_for(total_T);
 
-  uint64_t chunk = 4096;
-  while (chunk > 32 && total_T / chunk < 8 * resident_threads()) chunk >>= 1;
-
-  // pass 2: build the table (every odd N; skipped ones get no chunks) in
-  // small stack blocks; a copy from pageable memory has consumed its source
-  // when cudaMemcpyAsync returns, so the block can be refilled at once
-  constexpr size_t kBlock = 64;
-  SweepN stage[kBlock];
+  // pass 2: the table (every odd N; skipped ones get no chunks), in one copy
   uint64_t items = 0;
-  cudaError_t err = cudaSuccess;
-  for (size_t i0 = 0; i0 < n_odd && err == cudaSuccess; i0 += kBlock) {
-    const size_t nb = n_odd - i0 < kBlock ? n_odd - i0 : kBlock;
-    for (size_t j = 0; j < nb; ++j) {
-      uint64_t checked = 0;
-      noalloc_entry(variant, log2R, alpha, first + 2 * static_cast<int64_t>(i0 + j), flags, rules,
-                    &stage[j], &checked);
-      stage[j].item0 = items;
-      items += (checked + chunk - 1) / chunk;
-    }
-    err = cudaMemcpyAsync(d_tab + i0, stage, nb * sizeof(SweepN), cudaMemcpyHostToDevice, s);
+  for (size_t i = 0; i < n_odd; ++i) {
+    uint64_t checked = 0;
+    noalloc_entry(variant, log2R, alpha, first + 2 * static_cast<int64_t>(i), flags, rules,
+                  &g_noalloc_table[i], &checked);
+    g_noalloc_table[i].item0 = items;
+    items += (checked + chunk - 1) / chunk;
   }
+  cudaError_t err = cudaMemcpyAsync(d_tab, g_noalloc_table, n_odd * sizeof(SweepN),
+                                    cudaMemcpyHostToDevice, s);
   // counters start at zero on every call (the array keeps the last call's values)
   if (err == cudaSuccess) err = cudaMemsetAsync(d_counts, 0, n_odd * sizeof(unsigned long long), s);
   if (err == cudaSuccess) err = cudaMemsetAsync(d_cex_n, 0, sizeof(unsigned long long), s);
   SweepParams p{log2R, log2R / 2, alpha, static_cast<uint32_t>(chunk),
-                range_kind(variant, rules.range_rule)};
-  if (err == cudaSuccess) {
-    const int nt = static_cast<int>(n_odd);
-    switch (variant) {
-      case MONT_REDC: err = launch_sweep<MONT_REDC>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
-      case MONT_SIGNED: err = launch_sweep<MONT_SIGNED>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
-      case MONT_PLANTARD: err = launch_sweep<MONT_PLANTARD>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
-      case MONT_SIGNED_PLANTARD: err = launch_sweep<MONT_SIGNED_PLANTARD>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
-      default: err = launch_sweep<MONT_SIGNED_PLANTARD2>(d_tab, nt, items, p, d_counts, d_cex, d_cex_n, cex_cap, s); break;
-    }
-  }
+                range_kind(variant, rules.range_rule), 1u};
+  if (err == cudaSuccess)
+    err = launch_sweep(variant, d_tab, static_cast<int>(n_odd), 0, items, p, d_counts, d_cex,
+                       d_cex_n, cex_cap, s);
   unsigned long long h_cex_n = 0;
   if (err == cudaSuccess)
     err = cudaMemcpyAsync(per_N_counts, d_counts, n_odd * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);

@@ -44,6 +44,8 @@ LaunchShape tuned_shape(int width, int variant, int mode) {
   // multi-limb Algorithms 1-4 (one thread per element): 128-thread blocks at
   // the occupancy limit measured best (1024 bits: 0.39 against 0.36 Gmodmul/s)
   if (width > 64 && variant != MONT_REDC) d.threads = 128;
+  // multi-limb REDC: 0 = block size chosen from the element count (cios.cu)
+  if (width > 64 && variant == MONT_REDC) d.threads = 0;
   return d;
 }
 
@@ -103,7 +105,7 @@ bool shape_valid(int width, int mode, const LaunchShape& s) {
   if (mode == MONT_TUNE_MODE_BATCHED) {
     return (s.threads == 128 || s.threads == 256) && (s.unroll == 1 || s.unroll == 2 || s.unroll == 4);
   }
-  if (width > 64) return s.threads == 128 || s.threads == 256;
+  if (width > 64) return s.threads == 64 || s.threads == 128 || s.threads == 256;
   return (s.threads == 64 || s.threads == 128 || s.threads == 256 || s.threads == 512) &&
          (s.unroll == 1 || s.unroll == 2 || s.unroll == 4) &&
          (s.vec_bytes == 0 || s.vec_bytes == 16 || s.vec_bytes == 32) && s.blocks_per_sm >= 0;
@@ -200,7 +202,7 @@ extern "C" int mont_autotune(mont_ctx_t ctx, size_t n, int flags, void* stream) 
       }
     } else {
       for (int team : {1, 2, 4, 8, 16})
-        for (int th : {128, 256}) {
+        for (int th : {64, 128, 256}) {
           LaunchShape c;
           c.threads = th; c.team = team;
           cands.push_back(c);

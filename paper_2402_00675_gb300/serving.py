@@ -20,7 +20,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import (MONT_PLANTARD, MONT_REDC, MONT_SIGNED, Server, mont_ctx_create)
+from . import (MONT_ETIMEOUT, MONT_PLANTARD, MONT_REDC, MONT_SIGNED, Server, mont_ctx_create)
 
 _ELEM_BYTES = {32: 4, 64: 8, 256: 32}
 
@@ -111,6 +111,9 @@ def run_stream(server: Server, jobs, ctxs: Contexts, pools: Pools, ring: OutputR
     def retire(jid):
         r = server.wait(jid)
         results[jid] = r
+        if r["status"] == MONT_ETIMEOUT:   # the device may still write its region
+            while server.job_busy(jid):
+                time.sleep(0.001)
         ring.drop(jid)
 
     t0 = time.perf_counter()
@@ -136,8 +139,7 @@ def run_stream(server: Server, jobs, ctxs: Contexts, pools: Pools, ring: OutputR
         ids.append(jid)
     for jid in ids:
         if jid not in results:
-            results[jid] = server.wait(jid)
-            ring.drop(jid)
+            retire(jid)
     recs = []
     for jid in ids:
         r = results[jid]
@@ -147,18 +149,80 @@ def run_stream(server: Server, jobs, ctxs: Contexts, pools: Pools, ring: OutputR
     return recs
 
 
+def _percentiles(lat_ms):
+    if len(lat_ms) == 0:
+        return None, None
+    return float(np.percentile(lat_ms, 50)), float(np.percentile(lat_ms, 99))
+
+
 def summarise(recs) -> dict:
-    """p50 / p99 latency (submission to results in host memory) and throughput."""
+    """p50 / p99 latency (submission to results in host memory), for all jobs
+    and for modmul and sweep jobs apart, and throughput."""
     lat = np.array([r["t_done"] - r["t_submit"] for r in recs]) * 1e3
+    kinds = np.array([r["kind"] for r in recs])
     t_first = min(r["t_submit"] for r in recs)
     t_last = max(r["t_done"] for r in recs)
     modmuls = sum(r["n"] for r in recs if r["kind"] == "modmul")
     ok = sum(1 for r in recs if r["status"] == 0)
+    p50, p99 = _percentiles(lat)
+    m50, m99 = _percentiles(lat[kinds == "modmul"])
+    s50, s99 = _percentiles(lat[kinds == "sweep"])
     return {
         "jobs": len(recs), "ok": ok,
-        "sweep_jobs": sum(1 for r in recs if r["kind"] == "sweep"),
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "sweep_jobs": int((kinds == "sweep").sum()),
+        "p50_ms": p50, "p99_ms": p99,
+        "modmul_p50_ms": m50, "modmul_p99_ms": m99,
+        "sweep_p50_ms": s50, "sweep_p99_ms": s99,
         "mean_ms": float(lat.mean()), "makespan_s": t_last - t_first,
         "gmodmul_s": modmuls / (t_last - t_first) / 1e9,
         "jobs_per_s": len(recs) / (t_last - t_first),
     }
+
+
+def sweep_checks(variant: int, log2R: int, n_lo: int, count: int) -> int:
+    """(N, T) checks of a sweep job over `count` consecutive odd N from n_lo,
+    each algorithm on its own domain (moduli outside its condition skipped):
+    REDC R N; Algorithm 1 N R - 1 (|T| < N R / 2); Algorithm 2 N^2 + 1 for
+    N < 2^n / phi, n = log2R / 2."""
+    R = 1 << log2R
+    n = log2R // 2
+    total = 0
+    for i in range(count):
+        N = n_lo + 2 * i
+        if variant == MONT_REDC and N < R:
+            total += R * N
+        elif variant == MONT_SIGNED and 2 * N < R:
+            total += N * R - 1
+        elif variant == MONT_PLANTARD:
+            d = (1 << (n + 1)) - N
+            if d > 0 and 5 * N * N < d * d:
+                total += N * N + 1
+    return total
+
+
+def stream_bound(jobs, sweep_rate: dict, link_gbs: float, hbm_gbs: float,
+                 max_len: int) -> dict:
+    """A lower bound on the time the device needs for a job stream: the sweep
+    jobs' checks at the sweep's measured rates (checks/s per variant) plus the
+    modmul kernels' bytes at the HBM rate, against the host link moving every
+    modmul operand in and every product out (link_gbs each way, both
+    directions at once).  The copies overlap the kernels, so the bound is the
+    larger of the two."""
+    sweep_s = 0.0
+    kernel_s = 0.0
+    bytes_in = bytes_out = 0
+    for j in jobs:
+        if j.kind == "sweep":
+            sweep_s += sweep_checks(j.variant, 16, j.n_lo, j.length) / sweep_rate[j.variant]
+        else:
+            n = min(j.length, max_len)
+            eb = _ELEM_BYTES[j.width]
+            bytes_in += 2 * n * eb
+            bytes_out += n * eb
+            kernel_s += 3 * n * eb / (hbm_gbs * 1e9)
+    link_s = max(bytes_in, bytes_out) / (link_gbs * 1e9)
+    device_s = sweep_s + kernel_s
+    bound_s = max(device_s, link_s)
+    return {"sweep_device_s": round(sweep_s, 3), "modmul_kernel_s": round(kernel_s, 4),
+            "link_s": round(link_s, 3), "bound_s": round(bound_s, 3),
+            "jobs_per_s_bound": round(len(jobs) / bound_s, 1)}

@@ -129,6 +129,35 @@ def test_cios_ragged_misaligned_in_place(k):
                 assert ints_of(da, k) == want
 
 
+@pytest.mark.parametrize("k", [8, 32, 64])
+def test_cios_block_sizes_and_default_shape(k):
+    """64-, 128- and 256-thread blocks and the untuned size-dependent default
+    give the same products (several blocks and a ragged tail)."""
+    rnd = random.Random(700 + k)
+    N = moduli(k, rnd)[0]
+    ctx = mg.mont_ctx_create(N, 32 * k, 0)
+    n = 5 * 64 + 7
+    a = [rnd.randrange(N) for _ in range(n)]
+    b = [rnd.randrange(N) for _ in range(n)]
+    want = [o.mul_value(0, x, y, N, 32 * k) for x, y in zip(a, b)]
+    da, db = limbs_tensor(a, k), limbs_tensor(b, k)
+    for team in TEAMS[k]:
+        for threads in (64, 128, 256):
+            for mode in range(4):
+                mg.mont_tune_set(32 * k, 0, mode, {"threads": threads, "team": team})
+            out = torch.zeros(n * k, dtype=torch.uint32, device="cuda")
+            mg.mont_mul(ctx, da, db, out, n=n)
+            sync()
+            assert ints_of(out, k) == want, (k, team, threads)
+    for mode in range(4):
+        mg.mont_tune_set(32 * k, 0, mode, None)
+    assert mg.mont_tune_get(32 * k, 0, 0)["threads"] == 0
+    out = torch.zeros(n * k, dtype=torch.uint32, device="cuda")
+    mg.mont_mul(ctx, da, db, out, n=n)
+    sync()
+    assert ints_of(out, k) == want
+
+
 @pytest.mark.parametrize("bits,count", [(256, 1 << 22), (384, 1 << 21), (1024, 1 << 17),
                                         (2048, 1 << 15)])
 def test_cios_full_size_workloads(bits, count):

@@ -3,6 +3,7 @@ of the same jobs alone and the oracle; admission by device memory; refusal of
 oversized jobs; bounded waits."""
 
 import random
+import time
 
 import numpy as np
 import pytest
@@ -145,22 +146,87 @@ def test_oversized_job_refused_and_bounded_waits():
 
 
 def test_job_timeout_reports_and_server_recovers():
-    """A job that runs longer than the server's job timeout completes with
-    MONT_ETIMEOUT (no GPU fault is involved: the host stops waiting); the
-    server keeps serving other jobs."""
+    """A job that runs longer than its timeout completes with MONT_ETIMEOUT
+    (no GPU fault is involved: the host stops waiting).  Its buffers stay
+    busy until its device work ends; then the products are in `out`, the
+    arena region is given back and the server keeps serving."""
     N = sy.random_odd_modulus(2048, seed=8)
     ctx = mg.mont_ctx_create(N, 2048, 0)
-    n = 1 << 20          # 256 MiB per operand: several ms of copies and compute
-    a = torch.zeros(n * 64, dtype=torch.uint32).pin_memory()
+    n = 1 << 21          # 512 MiB per operand: copies and compute of well over 1 ms
+    one = np.zeros((n, 64), dtype=np.uint32)
+    one[:, 0] = 1
+    a = torch.from_numpy(one.reshape(-1)).pin_memory()
     out = torch.zeros_like(a).pin_memory()
-    srv = mg.Server(1 << 30, slots=1, job_timeout_ms=1)
+    budget = 3 * n * 64 * 4 + (1 << 20)
+    srv = mg.Server(budget, slots=1, job_timeout_ms=1)
     jid = srv.submit_modmul(ctx, a, a, out, n=n)
     r = srv.wait(jid, 60000)
     assert r["status"] == mg.MONT_ETIMEOUT
-    srv.close()
-    srv = mg.Server(1 << 26, slots=1)
-    small = torch.ones(8 * 64, dtype=torch.uint32).pin_memory()
+    assert srv.job_busy(jid)                   # the copies and the kernel still run
+    for _ in range(30000):
+        if not srv.job_busy(jid):
+            break
+        time.sleep(0.001)
+    assert not srv.job_busy(jid)
+    assert srv.query()["arena_free"] >= 3 * n * 64 * 4   # the region came back
+    want = np.array(sy.limbs_of(o.mul_value(0, 1, 1, N, 2048), 64), dtype=np.uint32)
+    assert (out.numpy().reshape(n, 64) == want).all()
+    # the same server runs the next job (with a timeout of its own)
+    small = torch.from_numpy(one[:8].reshape(-1).copy()).pin_memory()
     o2 = torch.zeros_like(small).pin_memory()
-    jid = srv.submit_modmul(ctx, small, small, o2, n=8)
+    jid = srv.submit_modmul(ctx, small, small, o2, n=8, timeout_ms=30000)
     assert srv.wait(jid, 30000)["status"] == 0
-    srv.close()
+    assert (o2.numpy().reshape(8, 64) == want).all()
+    assert srv.close() == mg.MONT_OK
+
+
+def test_straggler_region_is_reused_not_stalled():
+    """A timed-out job holds its arena region only while its device work runs:
+    a later job larger than every free piece waits for that region and then
+    runs, instead of stalling the queue."""
+    N = sy.random_odd_modulus(2048, seed=9)
+    ctx = mg.mont_ctx_create(N, 2048, 0)
+    unit = 1 << 19                                 # elements per job unit
+    nb = unit * 64 * 4                             # bytes per operand of one unit
+    srv = mg.Server(3 * (3 * nb) + 4096, slots=2)  # room for three units
+    one = np.zeros((2 * unit, 64), dtype=np.uint32)
+    one[:, 0] = 1
+    a = torch.from_numpy(one.reshape(-1)).pin_memory()
+    outs = [torch.zeros(2 * unit * 64, dtype=torch.uint32).pin_memory() for _ in range(3)]
+    x = srv.submit_modmul(ctx, a, a, outs[0], n=unit)
+    y = srv.submit_modmul(ctx, a, a, outs[1], n=unit, timeout_ms=1)
+    z = srv.submit_modmul(ctx, a, a, outs[2], n=2 * unit)
+    rx, ry, rz = srv.wait(x, 60000), srv.wait(y, 60000), srv.wait(z, 60000)
+    assert rx["status"] == 0 and rz["status"] == 0
+    assert ry["status"] in (0, mg.MONT_ETIMEOUT)
+    want = np.array(sy.limbs_of(o.mul_value(0, 1, 1, N, 2048), 64), dtype=np.uint32)
+    assert (outs[2].numpy().reshape(2 * unit, 64) == want).all()
+    assert srv.close() == mg.MONT_OK
+
+
+def test_sweep_jobs_bounded_and_scratch_from_arena():
+    """A sweep job's scratch counts against the arena (refused when larger
+    than the budget); a sweep past its timeout completes with MONT_ETIMEOUT
+    between its launches and its region comes back; an untimed sweep in the
+    same server equals mont_verify_sweep."""
+    tiny = mg.Server(4096, slots=1)
+    with pytest.raises(mg.MontError) as ei:
+        tiny.submit_sweep(o.REDC, 16, 0, 3, 4095, cex_cap=16)
+    assert ei.value.status == mg.MONT_ENOMEM
+    tiny.close()
+    srv = mg.Server(64 << 20, slots=2)
+    slow = srv.submit_sweep(o.REDC, 16, 0, 3073, 4095, cex_cap=16, timeout_ms=1)
+    r = srv.wait(slow, 60000)
+    assert r["status"] == mg.MONT_ETIMEOUT and "sweep" not in r
+    for _ in range(30000):
+        if not srv.job_busy(slow):
+            break
+        time.sleep(0.001)
+    assert not srv.job_busy(slow)
+    ok = srv.submit_sweep(o.SIGNED_PLANTARD2, 12, 0, 3, 63, cex_cap=4096)
+    got = srv.wait(ok, 60000)
+    assert got["status"] == 0
+    alone = mg.mont_verify_sweep(o.SIGNED_PLANTARD2, 12, 0, 3, 63, cex_cap=4096)
+    assert got["sweep"].counts == alone.counts and got["sweep"].examples == alone.examples
+    assert srv.query()["arena_free"] == 64 << 20      # every region came back
+    assert srv.close() == mg.MONT_OK
