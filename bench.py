@@ -559,6 +559,12 @@ def extra_sweep(mg, stream):
 # product in 32-bit multiply-adds (4 for a full or high product, 3 for a low
 # one) and 64-bit adds as 2: REDC 30, Plantard 26.
 NTT_BUTTERFLY_OPS = {(0, 32): 11, (2, 32): 8, (0, 64): 30, (2, 64): 26}
+# Limb products (32x32 -> 64, lo + hi = 1; a low or a high half alone = 1/3 or
+# 2/3, at the multiply pipe's rates) of one butterfly's twiddle product.
+# 32-bit: REDC y w (1), m = lo N' (1/3), hi(m N) (2/3); Plantard hi(a b'lo) (2/3),
+# lo(a b'hi) (1/3), (q + 1) N (1).  64-bit: REDC y w (4), m low 64 bits (5/3),
+# hi64(m N) (11/3); Plantard hi64(a b'lo) (11/3), lo64(a b'hi) (5/3), (q+1) N (4).
+NTT_BUTTERFLY_LIMB_PRODUCTS = {(0, 32): 2.0, (2, 32): 2.0, (0, 64): 28 / 3, (2, 64): 28 / 3}
 
 
 def extra_ntt(mg, stream, peak):
@@ -589,13 +595,17 @@ def extra_ntt(mg, stream, peak):
             ms_i = _events_ms(g, 20, stream)
             bfly = batch * (n // 2) * log2n
             ops = bfly * NTT_BUTTERFLY_OPS[(v, w)] / (ms_f * 1e-3)
+            lp = bfly * NTT_BUTTERFLY_LIMB_PRODUCTS[(v, w)] / (ms_f * 1e-3)
             gb = 2 * batch * n * (w // 8) / (ms_f * 1e-3) / 1e9
             out[f"n{n}_w{w}_{'redc' if v == 0 else 'plantard'}"] = {
                 "polys": batch, "forward_us": round(ms_f * 1e3, 1), "inverse_us": round(ms_i * 1e3, 1),
                 "gcoeff_s": round(batch * n / (ms_f * 1e-3) / 1e9, 1),
-                "roofline": {"bound": "alu", "achieved": round(ops / 1e12, 2),
-                             "peak": round(PEAKS["issue"] / 1e12, 2), "unit": "T int-ops/s",
-                             "frac": round(ops / PEAKS["issue"], 3), "hbm_frac": round(gb / peak, 3)}}
+                "roofline": {"bound": "alu", "achieved": round(lp / 1e12, 3),
+                             "peak": round(PEAKS["limb"] / 1e12, 3),
+                             "unit": "T limb-products/s (the twiddle products on the multiply pipe)",
+                             "frac": round(lp / PEAKS["limb"], 3),
+                             "issue_frac": round(ops / PEAKS["issue"], 3),
+                             "hbm_frac": round(gb / peak, 3)}}
             plan.close()
     for tag in ("n256_w32", "n1024_w64"):
         out[f"{tag}_plantard_speedup_over_redc"] = round(
@@ -703,7 +713,7 @@ def _product(xs):
     return p
 
 
-def extra_serving(mg, jobs_count, stream, peak, sweep=None):
+def extra_serving(mg, jobs_count, stream, peak):
     """Poisson stream of mixed jobs through the serving loop at full rate
     (capacity) and at 0.5x and 0.8x of the measured capacity, with the
     stream's lower-bound time (sweep checks at the measured sweep rates, the
@@ -723,13 +733,22 @@ def extra_serving(mg, jobs_count, stream, peak, sweep=None):
     h_out = ring.buf[: h_in.numel() * h_in.element_size()].view(h_in.dtype)
     link = measure_link(h_in, d_buf, h_out, d_buf, stream)
     del d_buf
+    # sweep rates as the jobs see them: one 512-moduli window per algorithm,
+    # alone (REDC and Algorithm 1 at the top of the range, where their
+    # windows spend most of their time; Algorithm 2 where its moduli are)
     rates = {}
-    names = {0: "redc", 1: "sigredc", 2: "predc"}
-    for v in (0, 1, 2):
-        key = f"{names[v]}_own_domain"
-        rates[v] = (sweep[key]["gchecks_s"] * 1e9) if sweep and key in sweep else 1e12
+    for v, lo in ((0, 3073), (1, 3073), (2, 3)):
+        mg.mont_verify_sweep(v, 16, 0, lo, lo + 1022, cex_cap=16, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = mg.mont_verify_sweep(v, 16, 0, lo, lo + 1022, cex_cap=16, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rates[v] = sum(r.checked.values()) / (e0.elapsed_time(e1) * 1e-3)
     bound = serving.stream_bound(jobs, rates, link["both_each_gbs"], peak, pools.max_len)
     bound["link"] = link
+    bound["sweep_gchecks_s"] = {k: round(v / 1e9, 1) for k, v in rates.items()}
     out["bound"] = bound
     cap = serving.summarise(serving.run_stream(server, jobs, ctxs, pools, ring, rate_scale=0.0))
     out["capacity"] = cap
@@ -900,7 +919,7 @@ def run_ours(args):
             "dot_lazy": extra_dot(mg, stream, peak),
             "rns_convert": extra_rns(mg, stream),
         }
-        extras["serving"] = extra_serving(mg, args.serving_jobs, stream, peak, extras["sweep_r16"])
+        extras["serving"] = extra_serving(mg, args.serving_jobs, stream, peak)
 
     result = None
     if rank == 0:
@@ -979,8 +998,10 @@ def config_summary(value, roof, ex):
     nt = ex["ntt"]
     rc = ex["rns_convert"]["roofline"]
     c["next"] = {
-        "ntt256_w32_plantard": nt["n256_w32_plantard"]["roofline"]["frac"],
-        "ntt1024_w64_plantard": nt["n1024_w64_plantard"]["roofline"]["frac"],
+        "ntt256_w32_plantard_mul_issue_hbm": [nt["n256_w32_plantard"]["roofline"][k]
+                                              for k in ("frac", "issue_frac", "hbm_frac")],
+        "ntt1024_w64_plantard_mul_issue_hbm": [nt["n1024_w64_plantard"]["roofline"][k]
+                                               for k in ("frac", "issue_frac", "hbm_frac")],
         "dot_lazy_hbm": ex["dot_lazy"]["roofline"]["frac"],
         "rns_to_from": [rc["frac_to"], rc["frac_from"]],
         "alg1to4": {w: [min(v["roofline"]["frac"] for k, v in lv.items() if k.startswith(w)),
@@ -1044,7 +1065,7 @@ def run_extras_only(names):
     out = {}
     for name in names:
         if name == "serving":
-            out[name] = extra_serving(mg, 10000, stream, peak, out.get("sweep_r16"))
+            out[name] = extra_serving(mg, 10000, stream, peak)
             continue
         fn = table[name]
         out[name] = fn(mg, stream, peak) if fn.__code__.co_argcount == 3 else fn(mg, stream)

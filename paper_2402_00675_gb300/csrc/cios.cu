@@ -145,14 +145,19 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
       for (int j = 0; j < S; ++j) bl[j] = bconst[j];
     }
 
+    // K iterations, as L rounds of S: round I takes b's limbs from the
+    // team's lane I.  Only a round is unrolled, so that the body stays in the
+    // instruction cache at 1024 and 2048 bits.
+#pragma unroll 1
+    for (int I = 0; I < L; ++I) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-      if constexpr (kProduct) {  // t += a * b_i
+    for (int s = 0; s < S; ++s) {
+      if constexpr (kProduct) {  // t += a * b_i, i = I S + s
         uint32_t bi;
         if constexpr (L == 1) {
-          bi = bl[i];
+          bi = bl[s];
         } else {
-          bi = __shfl_sync(kFull, bl[i % S], static_cast<int>(team_base + i / S));
+          bi = __shfl_sync(kFull, bl[s], static_cast<int>(team_base) + I);
         }
         mac_row<S>(t, h0, h1, al, bi);
       }
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
       t[S - 1] = top;
       h0 = h1 + (top < h0 ? 1u : 0u);
       h1 = 0;
+    }
     }
 
     // t = sum over lanes of (slice + h0 at position S).  REDC of a given T
@@ -239,9 +245,10 @@ cudaError_t launch_mode_kl(Mode mode, const LimbConst& c, const uint32_t* x, con
   return cudaErrorInvalidValue;
 }
 
-// Team size for a limb count: the tuned one if valid, else the default.
-// (2048 bits: 4 lanes tie 8 at 2^15 elements and are 8% faster at 2^17)
-int default_team(int k) { return k <= 16 ? 1 : 4; }
+// Team size for a limb count: the tuned one if valid, else the default
+// (measured: 1024 bits at 2^17 elements, 2 lanes 57.4 us against 61.5 for 4;
+// 2048 bits at 2^15, 4 lanes 62.8 us against 64.6 for 8 and 73.8 for 16).
+int default_team(int k) { return k <= 16 ? 1 : (k == 32 ? 2 : 4); }
 
 cudaError_t dispatch(int k, int team, Mode mode, const LimbConst& c, const uint32_t* x,
                      const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s, int vec16,
@@ -278,10 +285,10 @@ bool team_supported(int k, int team) {
   return false;
 }
 
-// Block size when none is tuned: 256 threads (measured: at 2^15 elements of
-// 2048 bits, four lanes each, 64-thread blocks spread the teams more evenly
-// over the SMs but ran 8% slower).
-int default_threads(int, int, size_t) { return 256; }
+// Block size when none is tuned: 256 threads, 128 for 2048 bits (measured at
+// 2^15 elements, four lanes each: 128 threads 62.8 us, 256 threads 63.5 us,
+// 64 threads 70.0 us).
+int default_threads(int k, int, size_t) { return k == 64 ? 128 : 256; }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

@@ -15,7 +15,8 @@
 //
 // A modmul job copies its host operands into its arena buffers, runs mont_mul
 // and copies the products back, on its worker's high-priority stream, in
-// pieces of 16 MiB per operand so that the copy engines interleave the jobs.  A
+// pieces of 16 MiB per operand, at most two in flight, so that the copies of
+// concurrent jobs interleave.  A
 // sweep job takes its table, counters and example buffer from the arena too
 // and runs on its worker's low-priority stream in launches of about 2^31
 // checks (a millisecond or two of the whole GPU), at most two in flight, so
@@ -239,11 +240,12 @@ Run finish(cudaStream_t s, Clock::time_point deadline, int enqueue_status) {
   return r;
 }
 
-// Bytes of one operand piece of a modmul job.  The copy engines serve the
-// streams' copies one command at a time, so a job's transfers are issued in
-// pieces: a small job then waits behind at most one piece of a large job's
-// copies, not behind all of them, and a large job's own copies overlap its
-// kernels.
+// Bytes of one operand piece of a modmul job.  A job's transfers are issued
+// in pieces, at most two in flight: the streams of the server share the
+// device's few hardware queues, and a job that enqueued all of its copies at
+// once would put a small job's commands behind all of them.  With bounded
+// pieces a small job waits behind at most a few pieces of a large one, and a
+// large job's own copies overlap its kernels.
 constexpr size_t kCopyPieceBytes = size_t{16} << 20;
 
 Run run_modmul(Job* j, char* dev, cudaStream_t s, Clock::time_point deadline) {
@@ -258,8 +260,17 @@ Run run_modmul(Job* j, char* dev, cudaStream_t s, Clock::time_point deadline) {
   const auto* ha = static_cast<const char*>(d.a);
   const auto* hb = static_cast<const char*>(d.b);
   auto* hout = static_cast<char*>(d.out);
+  cudaEvent_t inflight[2] = {nullptr, nullptr};
   int st = MONT_OK;
-  for (size_t e0 = 0; st == MONT_OK && e0 < d.n; e0 += piece) {
+  size_t k = 0;
+  for (size_t e0 = 0; st == MONT_OK && e0 < d.n; e0 += piece, ++k) {
+    cudaEvent_t& slot = inflight[k % 2];
+    if (slot) {  // two pieces back: wait for it before queueing another
+      st = wait_event(slot, deadline, 50);
+      cudaEventDestroy(slot);
+      slot = nullptr;
+      if (st != MONT_OK) break;
+    }
     const size_t cnt = d.n - e0 < piece ? d.n - e0 : piece;
     const size_t off = e0 * eb, bytes = cnt * eb;
     cudaError_t e = cudaMemcpyAsync(da + off, ha + off, bytes, cudaMemcpyHostToDevice, s);
@@ -271,8 +282,14 @@ Run run_modmul(Job* j, char* dev, cudaStream_t s, Clock::time_point deadline) {
     st = mont_mul(d.ctx, da + off, db + off, dout + off, cnt, s);
     if (st != MONT_OK) break;
     e = cudaMemcpyAsync(hout + off, dout + off, bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) st = cuda_status(e);
+    if (e != cudaSuccess) {
+      st = cuda_status(e);
+      break;
+    }
+    if (d.n - e0 > piece) st = record(s, &slot);   // no event after the last piece
   }
+  for (auto& ev : inflight)
+    if (ev) cudaEventDestroy(ev);
   // whatever was enqueued must finish before the region and buffers are free
   return finish(s, deadline, st);
 }

@@ -147,9 +147,10 @@ def test_oversized_job_refused_and_bounded_waits():
 
 def test_job_timeout_reports_and_server_recovers():
     """A job that runs longer than its timeout completes with MONT_ETIMEOUT
-    (no GPU fault is involved: the host stops waiting).  Its buffers stay
-    busy until its device work ends; then the products are in `out`, the
-    arena region is given back and the server keeps serving."""
+    (no GPU fault is involved: the host stops waiting, and stops issuing the
+    job's remaining pieces).  Its buffers stay busy until the device work
+    already issued ends; then a prefix of whole pieces holds correct products,
+    the arena region is given back and the server keeps serving."""
     N = sy.random_odd_modulus(2048, seed=8)
     ctx = mg.mont_ctx_create(N, 2048, 0)
     n = 1 << 21          # 512 MiB per operand: copies and compute of well over 1 ms
@@ -170,7 +171,14 @@ def test_job_timeout_reports_and_server_recovers():
     assert not srv.job_busy(jid)
     assert srv.query()["arena_free"] >= 3 * n * 64 * 4   # the region came back
     want = np.array(sy.limbs_of(o.mul_value(0, 1, 1, N, 2048), 64), dtype=np.uint32)
-    assert (out.numpy().reshape(n, 64) == want).all()
+    rows = out.numpy().reshape(n, 64)
+    done = (rows == want).all(axis=1)
+    untouched = (rows == 0).all(axis=1)
+    assert (done | untouched).all()
+    k = int(np.argmin(done)) if not done.all() else n          # written prefix
+    assert k > 0 and done[:k].all() and untouched[k:].all()
+    piece = (16 << 20) // (64 * 4)
+    assert k % piece == 0 or k == n
     # the same server runs the next job (with a timeout of its own)
     small = torch.from_numpy(one[:8].reshape(-1).copy()).pin_memory()
     o2 = torch.zeros_like(small).pin_memory()
