@@ -683,13 +683,15 @@ def extra_rns(mg, stream):
     # 32x32 -> 64-bit limb products (lo + hi) the algorithms need per element.
     # to_residues: each of the 32 residues sums limbs(X) limb-by-word products
     # (2 limb products each) and ends in one 64-bit REDC (about 12).
-    # from_residues, step i: the partial value has limbs(Pi_i) limbs; its
-    # residue (2 per limb), the digit (one 64-bit product and two REDCs, about
-    # 28) and the update by v_i Pi_i (2 per limb of Pi_i).
-    lx = -(-_product(ps).bit_length() // 32)
-    lpi = [-(-_product(ps[:i]).bit_length() // 32) if i else 1 for i in range(32)]
+    # from_residues (the CRT formula): xh_i M_i for every i (2 per limb of
+    # M_i = P / p_i), q' P (1 per limb of P), and per modulus xh_i by one
+    # 64-bit REDC of x_i times a constant (28/3) and the 64-bit fraction
+    # xh_i floor(2^128 / p_i) / 2^64 (16/3).
+    P = _product(ps)
+    lx = -(-P.bit_length() // 32)
     prods_to = 32 * (2 * lx + 12)
-    prods_from = sum(4 * l + 28 for l in lpi)
+    prods_from = round(sum(2 * -(-(P // p).bit_length() // 32) for p in ps) + lx
+                       + len(ps) * (28 / 3 + 16 / 3))
     r.close()
     a_to = n * prods_to / (ms_to * 1e-3)
     a_from = n * prods_from / (ms_from * 1e-3)

@@ -336,11 +336,13 @@ int mont_ntt_destroy(mont_ntt_t plan);
  * derives for two moduli from Qin's identity, Eq. (2), and states extends).
  *
  * mont_rns_create -- host array of `count` (1..64) odd, pairwise coprime
- *   moduli, 3 <= p < 2^63, with product P < 2^2048.  Precomputes the Montgomery
- *   constants (R = 2^64) and the partial products p_0 .. p_{i-1}, copied to a
- *   device allocation owned by the object (synchronous).  MONT_EINVAL otherwise.
+ *   moduli, 3 <= p < 2^63, with product P < 2^2047.  Precomputes the Montgomery
+ *   constants (R = 2^64), M_i = P / p_i with M_i^{-1} mod p_i, and floor(2^128 /
+ *   p_i), copied to a device allocation owned by the object (synchronous).
+ *   MONT_EINVAL otherwise.
  * mont_rns_query -- number of moduli, and `limbs`: the 32-bit limbs of every
- *   big integer these calls read or write (8, 16, 32 or 64; at least P's).
+ *   big integer these calls read or write (8, 16, 32 or 64: the least with
+ *   32 limbs > the bits of P).
  * mont_rns_to_residues -- residues[i n + e] = X_e mod p_i for n big integers X
  *   (element e at X[e limbs .. (e+1) limbs), little-endian, any value below
  *   2^(32 limbs)).  X 16-byte aligned, residues 8-byte aligned, not

@@ -16,16 +16,21 @@
 // (two mad.lo, two mad.hi, three addc) per limb product, reading one limb
 // per element and one broadcast 32-byte row of constants per limb.
 //
-// Residues -> big integer.  Mixed radix (Garner): X = sum_i v_i Pi_i with
-// Pi_i = p_0 ... p_{i-1} and v_i = (x_i - X_{<i}) Pi_i^{-1} mod p_i, where
-// X_{<i} = sum_{j<i} v_j Pi_j is the partial value already built.  One thread
-// per element keeps X in registers as 32-bit limbs; each step reduces X_{<i}
-// modulo p_i with the lazy accumulation above, forms v_i with one REDC
-// (Pi_i^{-1} kept in Montgomery form), and adds v_i Pi_i limb by limb.  Since
-// X_{<i} < Pi_i, both passes of step i run only over the limbs of Pi_i and
-// Pi_{i+1} (in blocks of four, a warp-uniform skip), about half of all.  The
-// result is the unique X in [0, P), P = prod p_i, with no quotient estimate
-// and no correction step.
+// Residues -> big integer: the CRT formula itself.  With M_i = P / p_i and
+// xh_i = x_i M_i^{-1} mod p_i, S = sum_i xh_i M_i is congruent to X modulo
+// every p_i and S / P = sum_i xh_i / p_i, so X = S - qP with q = floor(S/P).
+// q comes from 64-bit fractions f_i = floor(xh_i floor(2^128 / p_i) / 2^64)
+// <= xh_i 2^64 / p_i, each at most 2 below it: q' = floor(sum_i f_i / 2^64)
+// is q or q - 1, so S - q'P lies in [0, 2P) and one conditional subtraction
+// of P finishes.  S - q'P is formed in the same product as S, by one more
+// row q' (2^{32K} - P): its extra q' 2^{32K} falls above the K limbs kept.
+// The product is an (elements x moduli) by (moduli x limbs) matrix product,
+// tiled like the conversion above: a block takes 64 elements; warp w owns
+// limbs K/8 w .. K/8 (w+1) - 1 and lane l elements l and l + 32, each output
+// a 128-bit sum, with xh staged in shared memory as [modulus][element] and
+// M as [modulus][limb] (read as broadcasts).  Each thread then folds its
+// limbs into words plus a carry out of its group; one thread per element
+// adds the groups' carries in order and subtracts P if needed.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -119,94 +124,239 @@ __global__ void __launch_bounds__(256) rns_to_kernel(const uint32_t* __restrict_
   }
 }
 
-// Dynamic shared memory of the residues -> big kernel: the constants of
-// every step, staged once per block (the steps read them in lock step, so
-// every read is a broadcast).
-size_t from_smem_bytes(int K, int count) {
-  return static_cast<size_t>(count) * K * (sizeof(uint64_t) + sizeof(uint32_t)) +
-         static_cast<size_t>(count) * (sizeof(uint64_t) + sizeof(WordConst64)) +
-         static_cast<size_t>(count + 1) * sizeof(int);
+// The 128-bit value of four little-endian words.
+__device__ __forceinline__ u128 sum128(const uint32_t (&a)[4]) {
+  return (static_cast<u128>((static_cast<uint64_t>(a[3]) << 32) | a[2]) << 64) |
+         ((static_cast<uint64_t>(a[1]) << 32) | a[0]);
+}
+
+constexpr int kCrtGroups = 8;  // limb groups (one per warp)
+constexpr int kCrtEpt = 1;     // elements per thread: a block tile is 32 kCrtEpt elements
+
+// Dynamic shared memory of the reconstruction for K limbs and count moduli
+// (rows = count + 1, the last row being q' and 2^{32K} - P):
+//   ms [rows][K] uint32, xh [rows][T] uint64, st [T][K+1] uint32,
+//   ov [8 groups][4 words][T] uint32, fr [256 / T parts][2 words][T] uint64, P [K] uint32
+// for a tile of T = 32 kCrtEpt elements.
+size_t crt_smem_bytes(int K, int count) {
+  const size_t rows = static_cast<size_t>(count) + 1, T = 32 * kCrtEpt;
+  return rows * K * 4 + rows * T * 8 + T * (K + 1) * 4 + kCrtGroups * 4 * T * 4 + 256 * 2 * 8 +
+         static_cast<size_t>(K) * 4;
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) rns_from_kernel(const uint64_t* __restrict__ res,
-                                                       uint32_t* __restrict__ X, size_t n,
-                                                       int count,
-                                                       const WordConst64* __restrict__ mods,
-                                                       const uint64_t* __restrict__ c,
-                                                       const uint32_t* __restrict__ pi,
-                                                       const uint64_t* __restrict__ inv,
-                                                       const int* __restrict__ live) {
+__global__ void __launch_bounds__(256) rns_crt_kernel(const uint64_t* __restrict__ res,
+                                                      uint32_t* __restrict__ X, size_t n,
+                                                      int count,
+                                                      const WordConst64* __restrict__ mods,
+                                                      const uint64_t* __restrict__ cinv,
+                                                      const uint64_t* __restrict__ recip,
+                                                      const uint32_t* __restrict__ Mt,
+                                                      const uint32_t* __restrict__ Pl) {
+  constexpr int LPW = K / kCrtGroups;   // limbs of one warp
+  constexpr int kCrtTile = 32 * kCrtEpt;
+  constexpr int kParts = 256 / kCrtTile;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* cs = reinterpret_cast<uint64_t*>(smem);                      // count x K
-  WordConst64* ms = reinterpret_cast<WordConst64*>(cs + count * K);      // count
-  uint64_t* is = reinterpret_cast<uint64_t*>(ms + count);                // count
-  uint32_t* ps = reinterpret_cast<uint32_t*>(is + count);                // count x K
-  int* ls = reinterpret_cast<int*>(ps + count * K);                      // count + 1
-  for (int w = threadIdx.x; w < count * K; w += blockDim.x) {
-    cs[w] = c[w];
-    ps[w] = pi[w];
-  }
-  for (int w = threadIdx.x; w < count; w += blockDim.x) {
-    ms[w] = mods[w];
-    is[w] = inv[w];
-  }
-  for (int w = threadIdx.x; w <= count; w += blockDim.x) ls[w] = live[w];
-  __syncthreads();
-  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
-       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    uint32_t x[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) x[j] = 0;
-    uint64_t xi_next = res[e];
-    for (int i = 0; i < count; ++i) {
-      const uint64_t xi = xi_next;
-      if (i + 1 < count) xi_next = res[static_cast<size_t>(i + 1) * n + e];   // one step ahead
-      const WordConst64 m = ms[i];
-      const uint64_t* ci = cs + i * K;
-      const uint32_t* pii = ps + i * K;
-      // X_{<i} < Pi_i and X_{<i+1} < Pi_{i+1}: only their limbs can be non-zero
-      const int li = ls[i], ln = ls[i + 1];
-      // r = X_{<i} mod p_i, over the live limbs (blocks of 4; the skip is warp-uniform)
-      uint32_t a[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-      for (int q = 0; q < K / 4; ++q) {
-        if (4 * q < li) {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) mac_limb_word(a, x[4 * q + t], ci[4 * q + t]);
-        }
+  const int rows = count + 1;
+  uint32_t* ms = reinterpret_cast<uint32_t*>(smem);                   // [rows][K]
+  uint64_t* xh = reinterpret_cast<uint64_t*>(ms + rows * K);          // [rows][64]
+  uint32_t* st = reinterpret_cast<uint32_t*>(xh + rows * kCrtTile);   // [64][K+1]
+  uint32_t* ov = st + kCrtTile * (K + 1);                             // [8][4][64]
+  uint64_t* fr = reinterpret_cast<uint64_t*>(ov + kCrtGroups * 4 * kCrtTile);   // [parts][2][T]
+  uint32_t* ps = reinterpret_cast<uint32_t*>(fr + kParts * 2 * kCrtTile);  // [K]
+  for (int w = threadIdx.x; w < rows * K; w += blockDim.x) ms[w] = Mt[w];
+  for (int w = threadIdx.x; w < K; w += blockDim.x) ps[w] = Pl[w];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t tiles = (n + kCrtTile - 1) / kCrtTile;
+  for (size_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const size_t e0 = tile * kCrtTile;
+    __syncthreads();   // the previous tile is written out (and ms, ps are staged)
+    {  // xh_i = REDC(x_i (M_i^{-1} R mod p_i)) and the fractions, in parts of the moduli
+      const int e = threadIdx.x & (kCrtTile - 1), part = threadIdx.x / kCrtTile;
+      const bool valid = e0 + e < n;
+      u128 f = 0;
+      for (int i = part; i < count; i += kParts) {
+        const uint64_t x = valid ? res[static_cast<size_t>(i) * n + e0 + e] : 0u;
+        const uint64_t h = Redc64::reduce(static_cast<u128>(x) * cinv[i], mods[i]);
+        xh[i * kCrtTile + e] = h;
+        f += h * recip[2 * i + 1] + __umul64hi(h, recip[2 * i]);   // floor(h recip / 2^64) < 2^64
       }
-      const u128 T = (static_cast<u128>((static_cast<uint64_t>(a[3]) << 32) | a[2]) << 64) |
-                     ((static_cast<uint64_t>(a[1]) << 32) | a[0]);
-      const uint64_t r = Redc64::reduce(T, m);
-      const uint64_t d = xi >= r ? xi - r : xi + (m.N - r);
-      // v_i = (x_i - r) Pi_i^{-1} mod p_i   (is holds Pi_i^{-1} R mod p_i)
-      const uint64_t v = Redc64::reduce(static_cast<u128>(d) * is[i], m);
-      const uint32_t v0 = static_cast<uint32_t>(v), v1 = static_cast<uint32_t>(v >> 32);
-      // X += v Pi_i as two rows, v0 Pi_i and v1 Pi_i 2^32, in one pass over the
-      // limbs of Pi_{i+1} (row two lags one limb); each step is a 32x32 product
-      // plus two words, below 2^64, so the carries are single words
-      uint32_t ca = 0, cb = 0, p_prev = 0;
+      fr[(part * 2) * kCrtTile + e] = static_cast<uint64_t>(f);
+      fr[(part * 2 + 1) * kCrtTile + e] = static_cast<uint64_t>(f >> 64);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCrtTile) {   // q' = floor(sum of the fractions / 2^64): the last row
+      const int e = threadIdx.x;
+      u128 f = 0;
+      for (int part = 0; part < kParts; ++part)
+        f += (static_cast<u128>(fr[(part * 2 + 1) * kCrtTile + e]) << 64) | fr[(part * 2) * kCrtTile + e];
+      xh[count * kCrtTile + e] = static_cast<uint64_t>(f >> 64);
+    }
+    __syncthreads();
+    // S - q'P + q' 2^{32K} = sum over the rows of xh M: this warp's limbs,
+    // elements lane + 32 h
+    uint32_t acc[kCrtEpt][LPW][4];
 #pragma unroll
-      for (int q = 0; q < K / 4; ++q) {
-        if (4 * q < ln) {
+    for (int h = 0; h < kCrtEpt; ++h)
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int j = 4 * q + t;
-            const uint32_t p = pii[j];
-            const uint64_t s0 = static_cast<uint64_t>(v0) * p + x[j] + ca;
-            ca = static_cast<uint32_t>(s0 >> 32);
-            const uint64_t s1 = static_cast<uint64_t>(v1) * p_prev + static_cast<uint32_t>(s0) + cb;
-            cb = static_cast<uint32_t>(s1 >> 32);
-            x[j] = static_cast<uint32_t>(s1);
-            p_prev = p;
-          }
-        }
+      for (int jj = 0; jj < LPW; ++jj)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[h][jj][t] = 0u;
+#pragma unroll 4
+    for (int i = 0; i < rows; ++i) {
+      uint64_t v[kCrtEpt];
+#pragma unroll
+      for (int h = 0; h < kCrtEpt; ++h) v[h] = xh[i * kCrtTile + lane + 32 * h];
+      const uint32_t* mrow = ms + i * K + warp * LPW;
+#pragma unroll
+      for (int jj = 0; jj < LPW; ++jj) {
+        const uint32_t m = mrow[jj];
+#pragma unroll
+        for (int h = 0; h < kCrtEpt; ++h) mac_limb_word(acc[h][jj], m, v[h]);
       }
     }
-    uint4* out = reinterpret_cast<uint4*>(X + e * K);
+    // the group's limbs with the carries inside the group, and its carry out (< 2^72)
+    uint32_t lim[kCrtEpt][LPW];
 #pragma unroll
-    for (int j = 0; j < K / 4; ++j) out[j] = make_uint4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+    for (int h = 0; h < kCrtEpt; ++h) {
+      const int e = lane + 32 * h;
+      u128 pend = 0;
+#pragma unroll
+      for (int jj = 0; jj < LPW; ++jj) {
+        const u128 sum = sum128(acc[h][jj]) + pend;
+        lim[h][jj] = static_cast<uint32_t>(sum);
+        pend = sum >> 32;
+      }
+      ov[(warp * 4 + 0) * kCrtTile + e] = static_cast<uint32_t>(pend);
+      ov[(warp * 4 + 1) * kCrtTile + e] = static_cast<uint32_t>(pend >> 32);
+      ov[(warp * 4 + 2) * kCrtTile + e] = static_cast<uint32_t>(pend >> 64);
+    }
+    __syncthreads();
+    if constexpr (LPW >= 4) {
+      // Groups of at least 128 bits: a carry out below 2^72 added to a group
+      // leaves it at most one bit, so the groups settle in parallel with
+      // generate / propagate bits (a word of flags per group and element).
+      uint32_t* fl = st;   // [8 groups][64 elements] flags (st is free in this path)
+#pragma unroll
+      for (int h = 0; h < kCrtEpt; ++h) {
+        const int e = lane + 32 * h;
+        uint32_t gen = 0, all1 = 0xFFFFFFFFu;
+        if (warp > 0) {
+          u128 cin = (static_cast<u128>(ov[((warp - 1) * 4 + 2) * kCrtTile + e]) << 64) |
+                     (static_cast<u128>(ov[((warp - 1) * 4 + 1) * kCrtTile + e]) << 32) |
+                     ov[((warp - 1) * 4) * kCrtTile + e];
+#pragma unroll
+          for (int jj = 0; jj < LPW; ++jj) {
+            const u128 sum = static_cast<u128>(lim[h][jj]) + cin;
+            lim[h][jj] = static_cast<uint32_t>(sum);
+            cin = sum >> 32;
+          }
+          gen = static_cast<uint32_t>(cin);   // 0 or 1
+        }
+#pragma unroll
+        for (int jj = 0; jj < LPW; ++jj) all1 &= lim[h][jj];
+        fl[warp * kCrtTile + e] = gen | (all1 == 0xFFFFFFFFu ? 2u : 0u);
+      }
+      __syncthreads();
+      // the carry bit into this group, then X' >= P: compare the groups with P's
+      uint32_t take[kCrtEpt];
+#pragma unroll
+      for (int h = 0; h < kCrtEpt; ++h) {
+        const int e = lane + 32 * h;
+        uint32_t c = 0;
+        for (int g = 0; g < warp; ++g) {
+          const uint32_t f = fl[g * kCrtTile + e];
+          c = (f & 1u) | ((f >> 1) & c);
+        }
+        if (c) {
+#pragma unroll
+          for (int jj = 0; jj < LPW; ++jj) {   // + 1; the carry out was counted above
+            lim[h][jj] += c;
+            c = lim[h][jj] == 0u ? c : 0u;
+          }
+        }
+        // borrow of this group's limbs minus P's (generate) and equality (propagate)
+        uint32_t borrow = 0, eq = 1;
+#pragma unroll
+        for (int jj = 0; jj < LPW; ++jj) {
+          const uint32_t pj = ps[warp * LPW + jj];
+          const uint64_t d = static_cast<uint64_t>(lim[h][jj]) - pj - borrow;
+          borrow = static_cast<uint32_t>(d >> 63);
+          eq &= lim[h][jj] == pj ? 1u : 0u;
+        }
+        take[h] = borrow | (eq << 1);
+      }
+      __syncthreads();   // every group has read the carry flags
+#pragma unroll
+      for (int h = 0; h < kCrtEpt; ++h) fl[warp * kCrtTile + lane + 32 * h] = take[h];
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < kCrtEpt; ++h) {
+        const int e = lane + 32 * h;
+        if (e0 + e >= n) continue;
+        uint32_t b = 0, bin = 0;   // borrow into the top of every group; into this one
+        for (int g = 0; g < kCrtGroups; ++g) {
+          if (g == warp) bin = b;
+          const uint32_t f = fl[g * kCrtTile + e];
+          b = (f & 1u) | ((f >> 1) & b);
+        }
+        const uint32_t mask = b ? 0u : 0xFFFFFFFFu;   // no borrow out of the top: X' >= P
+        uint32_t borrow = bin & (mask & 1u);
+#pragma unroll
+        for (int jj = 0; jj < LPW; ++jj) {
+          const uint64_t d = static_cast<uint64_t>(lim[h][jj]) - (ps[warp * LPW + jj] & mask) - borrow;
+          lim[h][jj] = static_cast<uint32_t>(d);
+          borrow = static_cast<uint32_t>(d >> 63);
+        }
+        uint4* o = reinterpret_cast<uint4*>(X + (e0 + e) * K + warp * LPW);
+#pragma unroll
+        for (int q = 0; q < LPW / 4; ++q)
+          o[q] = make_uint4(lim[h][4 * q], lim[h][4 * q + 1], lim[h][4 * q + 2], lim[h][4 * q + 3]);
+      }
+    } else {
+      // narrow groups: one thread per element settles the carries in order
+#pragma unroll
+      for (int h = 0; h < kCrtEpt; ++h)
+#pragma unroll
+        for (int jj = 0; jj < LPW; ++jj) st[(lane + 32 * h) * (K + 1) + warp * LPW + jj] = lim[h][jj];
+      __syncthreads();
+      if (threadIdx.x < kCrtTile && e0 + threadIdx.x < n) {
+        const int e = threadIdx.x;
+        uint32_t* sv = st + e * (K + 1);
+        // carry each group's carry out into the groups above; what passes limb
+        // K - 1 is q' 2^{32K} (and nothing else, since S - q'P < 2P <= 2^{32K})
+        u128 pend = 0;
+        for (int g = 1; g < kCrtGroups; ++g) {
+          pend += (static_cast<u128>(ov[((g - 1) * 4 + 2) * kCrtTile + e]) << 64) |
+                  (static_cast<u128>(ov[((g - 1) * 4 + 1) * kCrtTile + e]) << 32) |
+                  ov[((g - 1) * 4) * kCrtTile + e];
+#pragma unroll
+          for (int jj = 0; jj < LPW; ++jj) {
+            const u128 sum = static_cast<u128>(sv[g * LPW + jj]) + pend;
+            sv[g * LPW + jj] = static_cast<uint32_t>(sum);
+            pend = sum >> 32;
+          }
+        }
+        // X' in [0, 2P): subtract P once if X' >= P
+        uint32_t borrow = 0;
+        for (int j = 0; j < K; ++j) {
+          const uint64_t d = static_cast<uint64_t>(sv[j]) - ps[j] - borrow;
+          borrow = static_cast<uint32_t>(d >> 63);
+        }
+        const uint32_t take = borrow ? 0u : 0xFFFFFFFFu;
+        borrow = 0;
+        for (int j = 0; j < K; ++j) {
+          const uint64_t d = static_cast<uint64_t>(sv[j]) - (ps[j] & take) - borrow;
+          sv[j] = static_cast<uint32_t>(d);
+          borrow = static_cast<uint32_t>(d >> 63);
+        }
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < kCrtTile * K; w += blockDim.x) {
+        const int e = w / K, j = w % K;
+        if (e0 + e < n) X[(e0 + e) * K + j] = st[e * (K + 1) + j];
+      }
+    }
   }
 }
 
@@ -250,11 +400,11 @@ cudaError_t launch_to(const uint32_t* X, uint64_t* res, size_t n, int count, con
 }
 
 template <int K>
-cudaError_t launch_from(const uint64_t* res, uint32_t* X, size_t n, int count,
-                        const WordConst64* mods, const uint64_t* c, const uint32_t* pi,
-                        const uint64_t* inv, const int* live, cudaStream_t s) {
-  const void* k = reinterpret_cast<const void*>(rns_from_kernel<K>);
-  const size_t smem = from_smem_bytes(K, count);
+cudaError_t launch_crt(const uint64_t* res, uint32_t* X, size_t n, int count,
+                       const WordConst64* mods, const uint64_t* cinv, const uint64_t* recip,
+                       const uint32_t* Mt, const uint32_t* Pl, cudaStream_t s) {
+  const void* k = reinterpret_cast<const void*>(rns_crt_kernel<K>);
+  const size_t smem = crt_smem_bytes(K, count);
   if (smem > 48u * 1024u) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
@@ -263,10 +413,10 @@ cudaError_t launch_from(const uint64_t* res, uint32_t* X, size_t n, int count,
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
   if (e != cudaSuccess) return e;
-  const size_t want = (n + 255) / 256;
+  const size_t tiles = (n + 32 * kCrtEpt - 1) / (32 * kCrtEpt);
   const size_t cap = static_cast<size_t>(device_sm_count()) * static_cast<size_t>(std::max(per_sm, 1));
-  rns_from_kernel<K><<<static_cast<unsigned>(std::min(want, cap)), 256, smem, s>>>(
-      res, X, n, count, mods, c, pi, inv, live);
+  rns_crt_kernel<K><<<static_cast<unsigned>(std::min(tiles, cap)), 256, smem, s>>>(
+      res, X, n, count, mods, cinv, recip, Mt, Pl);
   return cudaGetLastError();
 }
 
@@ -277,13 +427,14 @@ using namespace montgb;
 
 struct mont_rns {
   int count = 0;
-  int limbs = 0;                 // K: limbs of every big integer (>= those of P)
-  void* dev = nullptr;           // one allocation: mods, c, pi, inv
-  WordConst64* d_mods = nullptr;
-  uint64_t* d_c = nullptr;
-  uint32_t* d_pi = nullptr;
-  uint64_t* d_inv = nullptr;
-  int* d_live = nullptr;         // live[i] = limbs of Pi_i, i = 0..count
+  int limbs = 0;                 // K: limbs of every big integer (32 K > bits of P)
+  void* dev = nullptr;           // one allocation for every table below
+  WordConst64* d_mods = nullptr; // Montgomery constants of each p_i (R = 2^64)
+  uint64_t* d_c = nullptr;       // [count][K]: 2^{32 j} R mod p_i
+  uint64_t* d_cinv = nullptr;    // [count]: M_i^{-1} R mod p_i, M_i = P / p_i
+  uint64_t* d_recip = nullptr;   // [count][2]: floor(2^128 / p_i), low and high word
+  uint32_t* d_Mt = nullptr;      // [count + 1][K]: M_i, then 2^{32K} - P
+  uint32_t* d_P = nullptr;       // [K]: P
 };
 
 extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int count) {
@@ -310,17 +461,20 @@ extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int coun
     while (r.size() > 1 && r.back() == 0) r.pop_back();
     Pi[i + 1] = r;
   }
-  const int needed = static_cast<int>(Pi[count].size());
+  const std::vector<uint32_t>& P = Pi[count];
+  int bitsP = 32 * static_cast<int>(P.size());
+  for (uint32_t top = P.back(); !(top >> 31); top <<= 1) --bitsP;
   int K = 8;
-  while (K < needed) K *= 2;
-  if (K > 64) return MONT_EINVAL;   // P above 2^2048
+  while (32 * K <= bitsP) K *= 2;   // one spare bit: the reconstruction needs 2P < 2^{32K}
+  if (K > 64) return MONT_EINVAL;    // P of 2048 bits or more
 
   std::vector<WordConst64> mods(count);
   std::vector<uint64_t> c(static_cast<size_t>(count) * K);
-  std::vector<uint32_t> pi(static_cast<size_t>(count) * K, 0u);
-  std::vector<uint64_t> inv(count);
-  std::vector<int> live(count + 1);
-  for (int i = 0; i <= count; ++i) live[i] = static_cast<int>(Pi[i].size());
+  std::vector<uint64_t> cinv(count);
+  std::vector<uint64_t> recip(2 * static_cast<size_t>(count));
+  std::vector<uint32_t> Mt(static_cast<size_t>(count + 1) * K, 0u);
+  std::vector<uint32_t> Pl(K, 0u);
+  for (size_t j = 0; j < P.size(); ++j) Pl[j] = P[j];
   for (int i = 0; i < count; ++i) {
     const uint64_t p = moduli[i];
     WordConst64 m{};
@@ -338,37 +492,53 @@ extern "C" int mont_rns_create(mont_rns_t* out, const uint64_t* moduli, int coun
       c[static_cast<size_t>(i) * K + j] = cj;
       cj = mulmod64(cj, two32, p);
     }
-    for (size_t j = 0; j < Pi[i].size(); ++j) pi[static_cast<size_t>(i) * K + j] = Pi[i][j];
-    uint64_t pim = 1 % p;   // Pi_i mod p
-    for (int j = 0; j < i; ++j) pim = mulmod64(pim, moduli[j] % p, p);
-    inv[i] = mulmod64(invmod64(pim, p), r64, p);   // Montgomery form of Pi_i^{-1}
+    // M_i = P / p_i by long division over the limbs of P
+    u128h rem = 0;
+    for (int j = K - 1; j >= 0; --j) {
+      const u128h cur = (rem << 32) | Pl[j];
+      Mt[static_cast<size_t>(i) * K + j] = static_cast<uint32_t>(cur / p);
+      rem = cur % p;
+    }
+    uint64_t mm = 1 % p;   // M_i mod p_i = prod_{j != i} p_j mod p_i
+    for (int j = 0; j < count; ++j)
+      if (j != i) mm = mulmod64(mm, moduli[j] % p, p);
+    cinv[i] = mulmod64(invmod64(mm, p), r64, p);
+    const u128h rc = ~static_cast<u128h>(0) / p;   // floor((2^128 - 1) / p) = floor(2^128 / p)
+    recip[2 * static_cast<size_t>(i)] = static_cast<uint64_t>(rc);
+    recip[2 * static_cast<size_t>(i) + 1] = static_cast<uint64_t>(rc >> 64);
+  }
+  {  // the last row: 2^{32K} - P, two's complement of P over K limbs
+    uint64_t borrow = 0;
+    for (int j = 0; j < K; ++j) {
+      const uint64_t d = 0 - static_cast<uint64_t>(Pl[j]) - borrow;
+      Mt[static_cast<size_t>(count) * K + j] = static_cast<uint32_t>(d);
+      borrow = (d >> 32) & 1u;
+    }
   }
   mont_rns* r = new (std::nothrow) mont_rns;
   if (!r) return MONT_ENOMEM;
   r->count = count;
   r->limbs = K;
-  const size_t b_mods = count * sizeof(WordConst64);
-  const size_t b_c = c.size() * sizeof(uint64_t);
-  const size_t b_pi = pi.size() * sizeof(uint32_t);
-  const size_t b_inv = inv.size() * sizeof(uint64_t);
-  const size_t b_live = live.size() * sizeof(int);
-  const size_t off_c = (b_mods + 255) / 256 * 256;
-  const size_t off_pi = off_c + (b_c + 255) / 256 * 256;
-  const size_t off_inv = off_pi + (b_pi + 255) / 256 * 256;
-  const size_t off_live = off_inv + (b_inv + 255) / 256 * 256;
-  cudaError_t e = cudaMalloc(&r->dev, off_live + b_live);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_mods = count * sizeof(WordConst64), b_c = c.size() * 8, b_cinv = cinv.size() * 8,
+               b_recip = recip.size() * 8, b_Mt = Mt.size() * 4, b_P = Pl.size() * 4;
+  const size_t off_c = up(b_mods), off_cinv = off_c + up(b_c), off_recip = off_cinv + up(b_cinv),
+               off_Mt = off_recip + up(b_recip), off_P = off_Mt + up(b_Mt);
+  cudaError_t e = cudaMalloc(&r->dev, off_P + b_P);
   if (e == cudaSuccess) {
     char* base = static_cast<char*>(r->dev);
     r->d_mods = reinterpret_cast<WordConst64*>(base);
     r->d_c = reinterpret_cast<uint64_t*>(base + off_c);
-    r->d_pi = reinterpret_cast<uint32_t*>(base + off_pi);
-    r->d_inv = reinterpret_cast<uint64_t*>(base + off_inv);
-    r->d_live = reinterpret_cast<int*>(base + off_live);
+    r->d_cinv = reinterpret_cast<uint64_t*>(base + off_cinv);
+    r->d_recip = reinterpret_cast<uint64_t*>(base + off_recip);
+    r->d_Mt = reinterpret_cast<uint32_t*>(base + off_Mt);
+    r->d_P = reinterpret_cast<uint32_t*>(base + off_P);
     e = cudaMemcpy(r->d_mods, mods.data(), b_mods, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(r->d_c, c.data(), b_c, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(r->d_pi, pi.data(), b_pi, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(r->d_inv, inv.data(), b_inv, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(r->d_live, live.data(), b_live, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_cinv, cinv.data(), b_cinv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_recip, recip.data(), b_recip, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_Mt, Mt.data(), b_Mt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_P, Pl.data(), b_P, cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     if (r->dev) cudaFree(r->dev);
@@ -428,10 +598,10 @@ extern "C" int mont_rns_from_residues(mont_rns_t r, const uint64_t* residues, ui
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   switch (r->limbs) {
-    case 8: e = launch_from<8>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
-    case 16: e = launch_from<16>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
-    case 32: e = launch_from<32>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
-    default: e = launch_from<64>(residues, X, n, r->count, r->d_mods, r->d_c, r->d_pi, r->d_inv, r->d_live, s); break;
+    case 8: e = launch_crt<8>(residues, X, n, r->count, r->d_mods, r->d_cinv, r->d_recip, r->d_Mt, r->d_P, s); break;
+    case 16: e = launch_crt<16>(residues, X, n, r->count, r->d_mods, r->d_cinv, r->d_recip, r->d_Mt, r->d_P, s); break;
+    case 32: e = launch_crt<32>(residues, X, n, r->count, r->d_mods, r->d_cinv, r->d_recip, r->d_Mt, r->d_P, s); break;
+    default: e = launch_crt<64>(residues, X, n, r->count, r->d_mods, r->d_cinv, r->d_recip, r->d_Mt, r->d_P, s); break;
   }
   return cuda_status(e);
 }

@@ -53,7 +53,10 @@ def test_round_trip_and_definitions(idx):
     rnd = random.Random(idx)
     n = 1000
     X = [rnd.randrange(P) for _ in range(n)]
-    X[:3] = [0, 1, P - 1]
+    # small values (and 0, 1, P - 1): their CRT sums lie just above a multiple
+    # of P, where the quotient estimate is one short and P is subtracted
+    X[:10] = [0, 1, P - 1, 2, 3, (1 << 32) - 1, 1 << 32, (1 << 64) - 1, P - 2, P // 2]
+    X[:10] = [x % P for x in X[:10]]
     tX = limbs_tensor(X, k)
     res = torch.zeros(len(ps) * n, dtype=torch.uint64, device="cuda")
     r.to_residues(tX, res, n)
