@@ -496,10 +496,11 @@ def extra_limb_variants(mg, stream, peak):
             for _ in range(5):
                 f()
             ms = _events_ms(f, 20, stream)
-            # limb products as the kernel forms them: T = a b (k^2), then
-            # Algorithm 1: m low half (k(k+1)/2) and m N (k^2);
-            # Algorithms 2-4: m = T N^{-1} mod 2^{64k} (k(2k+1)) and q N ((k+1) k)
-            per = 2.5 * k * k + k / 2 if variant == 1 else 4 * k * k + 2 * k
+            # limb products as the kernels form them: Algorithm 1 on the CIOS
+            # schedule, 2k^2 + k (a b and m'N row by row, the k digits of m');
+            # Algorithms 2-4: T = a b (k^2), m = T N^{-1} mod 2^{64k} (k(2k+1))
+            # and q N ((k+1) k)
+            per = 2 * k * k + k if variant == 1 else 4 * k * k + 2 * k
             ach = per * count / (ms * 1e-3)
             out[f"{bits}b_{names[variant]}"] = {
                 "pairs": count, "gmodmul_s": round(count / (ms * 1e-3) / 1e9, 3),

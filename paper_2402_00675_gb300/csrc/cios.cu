@@ -27,6 +27,18 @@
 // computed from warp ballots (carry into lane l = bit l of
 // ((G << 1) + P) ^ P for generate mask G and propagate mask P), and the final
 // subtraction of N resolves its borrows the same way.
+//
+// Algorithm 1 (the signed Montgomery reduction) runs on the same schedule.
+// Its m = T N^{-1} mods R and CIOS's m' = -T N^{-1} mod R (the word-serial
+// digits m_i above) are congruent up to sign: m = -m' when m' <= R/2, else
+// m = R - m'.  So Algorithm 1's r = (T - mN)/R is (T + m'N)/R, less N when
+// m' > R/2.  Signed elements are k-limb two's complement integers A, B, read
+// as unsigned by the rows; for T = a b, A B = T + R (a [b < 0] + b [a < 0]) +
+// R^2 [a, b < 0], so modulo R (r lies in (-N, N), which k limbs hold)
+//   r = (A B + m'N)/R - [b < 0] A - [a < 0] B - [m' > R/2] N   (mod R),
+// three conditional subtractions with the same inter-lane borrow lookahead.
+// For a given 2k-limb T (mont_redc) the rows see T + R^2 [T < 0], which
+// changes nothing modulo R.
 #include <algorithm>
 
 #include "cios_chains.cuh"
@@ -97,9 +109,29 @@ __device__ __forceinline__ unsigned team_bits(bool x, unsigned team_base) {
   return (__ballot_sync(kFull, x) >> team_base) & mask;
 }
 
+// d <- d - (y & mask) modulo 2^{32k} over the team's slices: each lane
+// subtracts its slice, and the borrows between lanes resolve by lookahead.
+template <int S, int L>
+__device__ __forceinline__ void team_sub_masked(uint32_t (&d)[S], const uint32_t (&y)[S],
+                                                uint32_t mask, unsigned team_base, unsigned tl) {
+  uint32_t ym[S], r[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) ym[j] = y[j] & mask;
+  const uint32_t gb = sub_rows<S>(r, d, ym);
+  if constexpr (L > 1) {
+    const unsigned G = team_bits<L>(gb != 0, team_base);
+    const unsigned P = team_bits<L>(all_zero<S>(r), team_base);
+    const unsigned B = lookahead<L>(G, P);
+    if ((B >> tl) & 1u) sub_word<S>(r, 1u);
+  }
+#pragma unroll
+  for (int j = 0; j < S; ++j) d[j] = r[j];
+}
+
 // One element per team.  M: kMul (x*y), kToDomain (x * R^2 mod N),
-// kFromDomain (reduce x), kRedc (reduce the 2k-limb x).
-template <int K, int L, Mode M>
+// kFromDomain (reduce x), kRedc (reduce the 2k-limb x).  SIG: Algorithm 1
+// (signed elements; kMul, kToDomain and kRedc), else REDC.
+template <int K, int L, Mode M, bool SIG>
 __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ x,
                                                    const uint32_t* __restrict__ y,
                                                    uint32_t* __restrict__ out, size_t n,
@@ -117,7 +149,7 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
 #pragma unroll
   for (int j = 0; j < S; ++j) {
     nl[j] = c.N[tl * S + j];
-    bconst[j] = c.r2[tl * S + j];
+    bconst[j] = SIG ? c.dom[tl * S + j] : c.r2[tl * S + j];
   }
 
   for (size_t e0 = warp * TPW; e0 < n; e0 += nwarps * TPW) {
@@ -125,6 +157,7 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
     const bool valid = e < n;
     uint32_t al[S], bl[S], t[S], hi_in[S];
     uint32_t h0 = 0, h1 = 0;
+    uint32_t m_low = 0, m_top = 0;   // Algorithm 1: digits of m
 #pragma unroll
     for (int j = 0; j < S; ++j) { al[j] = 0; bl[j] = 0; t[j] = 0; hi_in[j] = 0; }
     if (valid) {
@@ -163,6 +196,10 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
       }
       uint32_t m = t[0] * c.n0prime;                     // exact on the team's lane 0
       if constexpr (L > 1) m = __shfl_sync(kFull, m, static_cast<int>(team_base));
+      if constexpr (SIG) {   // m' > R/2: its top digit, and whether any lower one is nonzero
+        if (I * S + s < K - 1) m_low |= m;
+        else m_top = m;
+      }
       mac_row<S>(t, h0, h1, nl, m);                      // t += m N; the low word is now 0
       uint32_t next0 = 0;                                // lowest limb of the lane above
       if constexpr (L > 1) {
@@ -198,6 +235,23 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
       top_word = __shfl_sync(kFull, h0, static_cast<int>(team_base + L - 1)) + carry_out;
     }
 
+    if constexpr (SIG) {
+      uint32_t d[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) d[j] = t[j];
+      (void)top_word;   // r is taken modulo R
+      if constexpr (kProduct) {
+        const uint32_t a_neg = (L == 1 ? al[S - 1] : __shfl_sync(kFull, al[S - 1], static_cast<int>(team_base + L - 1))) >> 31;
+        const uint32_t b_neg = (L == 1 ? bl[S - 1] : __shfl_sync(kFull, bl[S - 1], static_cast<int>(team_base + L - 1))) >> 31;
+        team_sub_masked<S, L>(d, al, 0u - b_neg, team_base, tl);   // - A if b < 0
+        team_sub_masked<S, L>(d, bl, 0u - a_neg, team_base, tl);   // - B if a < 0
+      }
+      const bool gt = m_top > 0x80000000u || (m_top == 0x80000000u && m_low != 0u);
+      team_sub_masked<S, L>(d, nl, gt ? 0xFFFFFFFFu : 0u, team_base, tl);   // - N if m' > R/2
+      if (valid) store_limbs<S>(out + e * K + tl * S, d, vec16);
+      continue;
+    }
+
     // one conditional subtraction of N (t < 2N)
     uint32_t d[S];
     const uint32_t gb = sub_rows<S>(d, t, nl);
@@ -219,28 +273,37 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
   }
 }
 
-template <int K, int L, Mode M>
+template <int K, int L, Mode M, bool SIG>
 cudaError_t launch_kl(const LimbConst& c, const uint32_t* x, const uint32_t* y, uint32_t* o,
                       size_t n, cudaStream_t s, int vec16, int threads) {
-  const void* k = reinterpret_cast<const void*>(cios_kernel<K, L, M>);
+  const void* k = reinterpret_cast<const void*>(cios_kernel<K, L, M, SIG>);
   const int per_sm = resident_blocks(k, threads);
   const size_t teams_per_block = static_cast<size_t>(threads) / L;
   const size_t want = (n + teams_per_block - 1) / teams_per_block;
   const size_t cap = static_cast<size_t>(device_sm_count()) * per_sm;
   const unsigned grid = static_cast<unsigned>(std::max<size_t>(1, std::min(want, cap)));
-  cios_kernel<K, L, M><<<grid, threads, 0, s>>>(x, y, o, n, c, vec16);
+  cios_kernel<K, L, M, SIG><<<grid, threads, 0, s>>>(x, y, o, n, c, vec16);
   return cudaGetLastError();
 }
 
 template <int K, int L>
-cudaError_t launch_mode_kl(Mode mode, const LimbConst& c, const uint32_t* x, const uint32_t* y,
-                           uint32_t* o, size_t n, cudaStream_t s, int vec16, int threads) {
+cudaError_t launch_mode_kl(Mode mode, bool sig, const LimbConst& c, const uint32_t* x,
+                           const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s, int vec16,
+                           int threads) {
+  if (sig) {
+    switch (mode) {
+      case Mode::kMul: return launch_kl<K, L, Mode::kMul, true>(c, x, y, o, n, s, vec16, threads);
+      case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain, true>(c, x, y, o, n, s, vec16, threads);
+      case Mode::kRedc: return launch_kl<K, L, Mode::kRedc, true>(c, x, y, o, n, s, vec16, threads);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (mode) {
-    case Mode::kMul: return launch_kl<K, L, Mode::kMul>(c, x, y, o, n, s, vec16, threads);
-    case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain>(c, x, y, o, n, s, vec16, threads);
+    case Mode::kMul: return launch_kl<K, L, Mode::kMul, false>(c, x, y, o, n, s, vec16, threads);
+    case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain, false>(c, x, y, o, n, s, vec16, threads);
     case Mode::kFromDomain:
-      return launch_kl<K, L, Mode::kFromDomain>(c, x, y, o, n, s, vec16, threads);
-    case Mode::kRedc: return launch_kl<K, L, Mode::kRedc>(c, x, y, o, n, s, vec16, threads);
+      return launch_kl<K, L, Mode::kFromDomain, false>(c, x, y, o, n, s, vec16, threads);
+    case Mode::kRedc: return launch_kl<K, L, Mode::kRedc, false>(c, x, y, o, n, s, vec16, threads);
   }
   return cudaErrorInvalidValue;
 }
@@ -250,11 +313,11 @@ cudaError_t launch_mode_kl(Mode mode, const LimbConst& c, const uint32_t* x, con
 // 2048 bits at 2^15, 4 lanes 62.8 us against 64.6 for 8 and 73.8 for 16).
 int default_team(int k) { return k <= 16 ? 1 : (k == 32 ? 2 : 4); }
 
-cudaError_t dispatch(int k, int team, Mode mode, const LimbConst& c, const uint32_t* x,
+cudaError_t dispatch(int k, int team, Mode mode, bool sig, const LimbConst& c, const uint32_t* x,
                      const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s, int vec16,
                      int threads) {
 #define MONTGB_KL(K_, L_) \
-  if (k == K_ && team == L_) return launch_mode_kl<K_, L_>(mode, c, x, y, o, n, s, vec16, threads);
+  if (k == K_ && team == L_) return launch_mode_kl<K_, L_>(mode, sig, c, x, y, o, n, s, vec16, threads);
   MONTGB_KL(4, 1)
   MONTGB_KL(8, 1)
   MONTGB_KL(8, 2)
@@ -309,7 +372,11 @@ int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y,
     const uintptr_t yo = reinterpret_cast<uintptr_t>(y);
     if (yo != oo && yo < oo + n * esize && oo < yo + n * esize) return MONT_EINVAL;
   }
-  if (ctx->variant != MONT_REDC) {   // Algorithms 1-4 (limb_variants.cu)
+  // Algorithm 1's products and reductions run on the CIOS schedule (see the
+  // top of this file); its from_domain, which also canonicalises, and
+  // Algorithms 2-4 run in limb_variants.cu
+  const bool sig = ctx->variant == MONT_SIGNED && mode != Mode::kFromDomain;
+  if (ctx->variant != MONT_REDC && !sig) {   // limb_variants.cu
     const int v16 = aligned(x, 16) && aligned(out, 16) && (!y || aligned(y, 16)) ? 1 : 0;
     return cuda_status(launch_limb_variant(k, mode, ctx->limbv, static_cast<const uint32_t*>(x),
                                            static_cast<const uint32_t*>(y),
@@ -324,7 +391,7 @@ int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y,
   int threads = shape.threads;
   if (threads != 64 && threads != 128 && threads != 256) threads = default_threads(k, team, n);
   const int vec16 = aligned(x, 16) && aligned(out, 16) && (!y || aligned(y, 16)) ? 1 : 0;
-  const cudaError_t e = dispatch(k, team, mode, ctx->limb, static_cast<const uint32_t*>(x),
+  const cudaError_t e = dispatch(k, team, mode, sig, ctx->limb, static_cast<const uint32_t*>(x),
                                  static_cast<const uint32_t*>(y), static_cast<uint32_t*>(out), n,
                                  static_cast<cudaStream_t>(stream), vec16, threads);
   return cuda_status(e);

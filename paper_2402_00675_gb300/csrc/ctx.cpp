@@ -236,6 +236,7 @@ extern "C" int mont_ctx_create(mont_ctx_t* out, const uint32_t* N_limbs, int n_l
     for (int i = 0; i < n_limbs; ++i) {
       k.N[i] = N[i];
       k.r2[i] = c->r2_mod_n[i];
+      k.dom[i] = c->domain_r2[i];
     }
     auto& v = c->limbv;
     v.variant = variant;

@@ -44,6 +44,7 @@ struct LimbConst {
   uint32_t n0prime;             // -N^{-1} mod 2^32: the only inverse CIOS needs
   uint32_t N[MONT_MAX_LIMBS];   // modulus, little-endian limbs (k used)
   uint32_t r2[MONT_MAX_LIMBS];  // R^2 mod N
+  uint32_t dom[MONT_MAX_LIMBS]; // Algorithm 1's domain constant: (R^2 mod N) mods N, two's complement
 };
 
 // Constants of one modulus for the multi-limb kernels of Algorithms 1-4

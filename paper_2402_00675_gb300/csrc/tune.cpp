@@ -44,8 +44,9 @@ LaunchShape tuned_shape(int width, int variant, int mode) {
   // multi-limb Algorithms 1-4 (one thread per element): 128-thread blocks at
   // the occupancy limit measured best (1024 bits: 0.39 against 0.36 Gmodmul/s)
   if (width > 64 && variant != MONT_REDC) d.threads = 128;
-  // multi-limb REDC: 0 = block size chosen from the element count (cios.cu)
-  if (width > 64 && variant == MONT_REDC) d.threads = 0;
+  // multi-limb REDC and Algorithm 1 (both on the CIOS schedule): 0 = the block
+  // size follows the limb count (cios.cu)
+  if (width > 64 && (variant == MONT_REDC || variant == MONT_SIGNED)) d.threads = 0;
   return d;
 }
 
@@ -192,8 +193,8 @@ extern "C" int mont_autotune(mont_ctx_t ctx, size_t n, int flags, void* stream) 
             c.threads = th; c.unroll = u; c.vec_bytes = vb;
             cands.push_back(c);
           }
-    } else if (ctx->variant != MONT_REDC) {
-      // Algorithms 1-4 at multi-limb widths: one thread per element, so the
+    } else if (ctx->variant != MONT_REDC && ctx->variant != MONT_SIGNED) {
+      // Algorithms 2-4 at multi-limb widths: one thread per element, so the
       // block size is the only choice
       for (int th : {128, 256}) {
         LaunchShape c;
