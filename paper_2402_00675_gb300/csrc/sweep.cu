@@ -238,9 +238,14 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
   uint32_t c[4] = {c0, c1, c2, c3};
   uint32_t local = 0;
   uint32_t i = 0;
+  // With the unsigned range the only good value is c itself, so the four
+  // checks of a step fold into one word: the OR of r ^ c (one three-input
+  // logic operation per check), tested once per step.
+  constexpr bool kFold = (V == MONT_REDC && RK == kUnsigned);
   for (; i + 4 <= cnt; i += 4) {
     int32_t r[4];
     bool g[4];
+    uint32_t diff = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t T = mad_lo(i, one, Tb[j]);
@@ -252,9 +257,14 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
         r[j] = (static_cast<int32_t>(T) >> L) -
                __mulhi(static_cast<int32_t>(u), static_cast<int32_t>(N));
       }
-      g[j] = fast_good<RK>(r[j], c[j], e);
+      if constexpr (kFold) diff |= static_cast<uint32_t>(r[j]) ^ c[j];
+      else g[j] = fast_good<RK>(r[j], c[j], e);
     }
-    if (!(g[0] && g[1] && g[2] && g[3])) {
+    if (kFold ? diff != 0u : !(g[0] && g[1] && g[2] && g[3])) {
+      if constexpr (kFold) {   // the rare step with a mismatch: which checks
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g[j] = static_cast<uint32_t>(r[j]) == c[j];
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (!g[j] && exact_bad(r[j], c[j], e)) {
