@@ -275,9 +275,10 @@ __global__ void __launch_bounds__(256) cios_kernel(const uint32_t* __restrict__ 
 
 template <int K, int L, Mode M, bool SIG>
 cudaError_t launch_kl(const LimbConst& c, const uint32_t* x, const uint32_t* y, uint32_t* o,
-                      size_t n, cudaStream_t s, int vec16, int threads) {
+                      size_t n, cudaStream_t s, int vec16, int threads, int bps) {
   const void* k = reinterpret_cast<const void*>(cios_kernel<K, L, M, SIG>);
-  const int per_sm = resident_blocks(k, threads);
+  const int resident = resident_blocks(k, threads);
+  const int per_sm = bps > 0 ? std::min(bps, resident) : resident;
   const size_t teams_per_block = static_cast<size_t>(threads) / L;
   const size_t want = (n + teams_per_block - 1) / teams_per_block;
   const size_t cap = static_cast<size_t>(device_sm_count()) * per_sm;
@@ -289,21 +290,21 @@ cudaError_t launch_kl(const LimbConst& c, const uint32_t* x, const uint32_t* y, 
 template <int K, int L>
 cudaError_t launch_mode_kl(Mode mode, bool sig, const LimbConst& c, const uint32_t* x,
                            const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s, int vec16,
-                           int threads) {
+                           int threads, int bps) {
   if (sig) {
     switch (mode) {
-      case Mode::kMul: return launch_kl<K, L, Mode::kMul, true>(c, x, y, o, n, s, vec16, threads);
-      case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain, true>(c, x, y, o, n, s, vec16, threads);
-      case Mode::kRedc: return launch_kl<K, L, Mode::kRedc, true>(c, x, y, o, n, s, vec16, threads);
+      case Mode::kMul: return launch_kl<K, L, Mode::kMul, true>(c, x, y, o, n, s, vec16, threads, bps);
+      case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain, true>(c, x, y, o, n, s, vec16, threads, bps);
+      case Mode::kRedc: return launch_kl<K, L, Mode::kRedc, true>(c, x, y, o, n, s, vec16, threads, bps);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (mode) {
-    case Mode::kMul: return launch_kl<K, L, Mode::kMul, false>(c, x, y, o, n, s, vec16, threads);
-    case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain, false>(c, x, y, o, n, s, vec16, threads);
+    case Mode::kMul: return launch_kl<K, L, Mode::kMul, false>(c, x, y, o, n, s, vec16, threads, bps);
+    case Mode::kToDomain: return launch_kl<K, L, Mode::kToDomain, false>(c, x, y, o, n, s, vec16, threads, bps);
     case Mode::kFromDomain:
-      return launch_kl<K, L, Mode::kFromDomain, false>(c, x, y, o, n, s, vec16, threads);
-    case Mode::kRedc: return launch_kl<K, L, Mode::kRedc, false>(c, x, y, o, n, s, vec16, threads);
+      return launch_kl<K, L, Mode::kFromDomain, false>(c, x, y, o, n, s, vec16, threads, bps);
+    case Mode::kRedc: return launch_kl<K, L, Mode::kRedc, false>(c, x, y, o, n, s, vec16, threads, bps);
   }
   return cudaErrorInvalidValue;
 }
@@ -315,9 +316,9 @@ int default_team(int k) { return k <= 16 ? 1 : (k == 32 ? 2 : 4); }
 
 cudaError_t dispatch(int k, int team, Mode mode, bool sig, const LimbConst& c, const uint32_t* x,
                      const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s, int vec16,
-                     int threads) {
+                     int threads, int bps) {
 #define MONTGB_KL(K_, L_) \
-  if (k == K_ && team == L_) return launch_mode_kl<K_, L_>(mode, sig, c, x, y, o, n, s, vec16, threads);
+  if (k == K_ && team == L_) return launch_mode_kl<K_, L_>(mode, sig, c, x, y, o, n, s, vec16, threads, bps);
   MONTGB_KL(4, 1)
   MONTGB_KL(8, 1)
   MONTGB_KL(8, 2)
@@ -357,6 +358,8 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 
 }  // namespace
 
+bool multilimb_team_supported(int k, int team) { return team_supported(k, team); }
+
 int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y, void* out,
                         size_t n, void* stream) {
   const int k = ctx->n_limbs;
@@ -393,7 +396,8 @@ int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y,
   const int vec16 = aligned(x, 16) && aligned(out, 16) && (!y || aligned(y, 16)) ? 1 : 0;
   const cudaError_t e = dispatch(k, team, mode, sig, ctx->limb, static_cast<const uint32_t*>(x),
                                  static_cast<const uint32_t*>(y), static_cast<uint32_t*>(out), n,
-                                 static_cast<cudaStream_t>(stream), vec16, threads);
+                                 static_cast<cudaStream_t>(stream), vec16, threads,
+                                 shape.blocks_per_sm);
   return cuda_status(e);
 }
 

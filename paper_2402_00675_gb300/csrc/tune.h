@@ -21,5 +21,8 @@ void set_tuned_batched_shape(int width, const LaunchShape& shape);
 // Multi-limb element-wise operations (cios.cu).
 int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y, void* out,
                         size_t n, void* stream);
+// Whether the multi-limb REDC kernels have a build for k limbs at this many
+// lanes per element (others run at the default team).
+bool multilimb_team_supported(int k, int team);
 
 }  // namespace montgb

@@ -158,16 +158,42 @@ def test_cios_block_sizes_and_default_shape(k):
     assert ints_of(out, k) == want
 
 
+@pytest.mark.parametrize("k", [32, 64])
+def test_cios_grid_capped_by_blocks_per_sm(k):
+    """A grid capped at 1, 2 or 3 blocks per SM walks the elements in more
+    rounds per warp and gives the same products (every element checked)."""
+    count = (1 << 16) // k * 8 + 5
+    N = sy.random_odd_modulus(32 * k, seed=12)
+    a = sy.uniform_limb_residues(N, k, count, seed=13)
+    b = sy.uniform_limb_residues(N, k, count, seed=14)
+    ctx = mg.mont_ctx_create(N, 32 * k, 0)
+    want = bulk.mul_value_obj(0, bulk.ints_from_limbs(a, k), bulk.ints_from_limbs(b, k), N, 32 * k)
+    da, db = torch.from_numpy(a.reshape(-1)).cuda(), torch.from_numpy(b.reshape(-1)).cuda()
+    for team in TEAMS[k]:
+        for bps in (1, 2, 3):
+            mg.mont_tune_set(32 * k, 0, 0, {"threads": 128, "team": team, "blocks_per_sm": bps})
+            out = torch.zeros(count * k, dtype=torch.uint32, device="cuda")
+            mg.mont_mul(ctx, da, db, out, n=count)
+            sync()
+            bad = np.flatnonzero(bulk.ints_from_limbs(out.cpu().numpy(), k) != want)
+            assert bad.size == 0, (k, team, bps, bad[:5])
+
+
+@pytest.mark.parametrize("tuned", [False, True], ids=["default_shape", "autotuned"])
 @pytest.mark.parametrize("bits,count", [(256, 1 << 22), (384, 1 << 21), (1024, 1 << 17),
                                         (2048, 1 << 15)])
-def test_cios_full_size_workloads(bits, count):
-    """The multi-limb benchmark sizes, default launch shape: every element
-    against the definition T R^{-1} mod N (Python integers)."""
+def test_cios_full_size_workloads(bits, count, tuned):
+    """The multi-limb benchmark sizes, at the built-in launch shape and at the
+    shape the autotuner picks for that size (the one the benchmark times):
+    every element against the definition T R^{-1} mod N (Python integers)."""
     k = bits // 32
     N = sy.random_odd_modulus(bits, seed=4)
     a = sy.uniform_limb_residues(N, k, count, seed=40 + k)
     b = sy.uniform_limb_residues(N, k, count, seed=80 + k)
     ctx = mg.mont_ctx_create(N, 32 * k, 0)
+    if tuned:
+        mg.mont_autotune(ctx, count)
+        assert mg.mont_tune_get(bits, 0, 0)["team"] in TEAMS[k]
     out = torch.empty(count * k, dtype=torch.uint32, device="cuda")
     mg.mont_mul(ctx, torch.from_numpy(a.reshape(-1)).cuda(), torch.from_numpy(b.reshape(-1)).cuda(),
                 out, n=count)
