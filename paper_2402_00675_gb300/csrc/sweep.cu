@@ -224,30 +224,42 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
   const uint32_t N = static_cast<uint32_t>(e.N);
   const uint32_t one = p.one;
   const uint32_t negN = 0u - N;
-  const uint32_t s4m = s4 - N;                   // s4 - N mod 2^32
   const int L = p.log2R;
   const uint32_t mask = (1u << L) - 1u;
   const uint32_t k = V == MONT_REDC ? e.nprime : e.ninv << (32 - L);
   const uint32_t T0w = static_cast<uint32_t>(static_cast<int32_t>(T0));
-  uint32_t Tb[4], kb[4];
+  // With the unsigned range the only good value is c itself, so the checks
+  // of a step fold into one word: the OR of r ^ c (one three-input logic
+  // operation per check), tested once per step.
+  constexpr bool kFold = (V == MONT_REDC && RK == kUnsigned);
+  // W chains per step: the step's fixed cost (loop test, mismatch test,
+  // branches) is shared by W checks.  Chain j >= 4 starts four steps of s
+  // after chain j - 4; every chain steps by sW = W s mod N.  (Eight chains
+  // for the folded REDC check; Algorithm 1's wider check runs four, as eight
+  // cost it more registers than the shared step saves.)
+  constexpr int W = kFold ? 8 : 4;
+  uint32_t Tb[W], kb[W];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < W; ++j) {
     Tb[j] = T0w + static_cast<uint32_t>(j);
     kb[j] = Tb[j] * k;
   }
-  uint32_t c[4] = {c0, c1, c2, c3};
+  uint32_t c[W];
+  c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;
+#pragma unroll
+  for (int j = 4; j < W; ++j) c[j] = step_ref<RK>(c[j - 4], s4, N);
+  uint32_t sW = s4;                                    // W s mod N, in [0, N)
+#pragma unroll
+  for (int w = 4; w < W; w *= 2) sW = step_ref<kUnsigned>(sW, sW, N);
+  const uint32_t sWm = sW - N;
   uint32_t local = 0;
   uint32_t i = 0;
-  // With the unsigned range the only good value is c itself, so the four
-  // checks of a step fold into one word: the OR of r ^ c (one three-input
-  // logic operation per check), tested once per step.
-  constexpr bool kFold = (V == MONT_REDC && RK == kUnsigned);
-  for (; i + 4 <= cnt; i += 4) {
-    int32_t r[4];
-    bool g[4];
+  for (; i + W <= cnt; i += W) {
+    int32_t r[W];
+    bool g[W];
     uint32_t diff = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < W; ++j) {
       const uint32_t T = mad_lo(i, one, Tb[j]);
       const uint32_t u = mad_lo(i, k, kb[j]);            // T k mod 2^32
       if constexpr (V == MONT_REDC) {
@@ -260,13 +272,18 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
       if constexpr (kFold) diff |= static_cast<uint32_t>(r[j]) ^ c[j];
       else g[j] = fast_good<RK>(r[j], c[j], e);
     }
-    if (kFold ? diff != 0u : !(g[0] && g[1] && g[2] && g[3])) {
+    bool all_good = true;
+    if constexpr (!kFold) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) all_good = all_good && g[j];
+    }
+    if (kFold ? diff != 0u : !all_good) {
       if constexpr (kFold) {   // the rare step with a mismatch: which checks
 #pragma unroll
-        for (int j = 0; j < 4; ++j) g[j] = static_cast<uint32_t>(r[j]) == c[j];
+        for (int j = 0; j < W; ++j) g[j] = static_cast<uint32_t>(r[j]) == c[j];
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < W; ++j) {
         if (!g[j] && exact_bad(r[j], c[j], e)) {
           ++local;
           if (!full)
@@ -276,11 +293,11 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < W; ++j) {
       if constexpr (RK == kCentred) {
-        c[j] = step_ref<RK>(c[j], s4, N);
+        c[j] = step_ref<RK>(c[j], sW, N);
       } else {
-        c[j] = min(mad_lo(c[j], one, s4), mad_lo(c[j], one, s4m));
+        c[j] = min(mad_lo(c[j], one, sW), mad_lo(c[j], one, sWm));
       }
     }
   }
