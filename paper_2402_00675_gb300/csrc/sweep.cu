@@ -228,15 +228,25 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
   const uint32_t mask = (1u << L) - 1u;
   const uint32_t k = V == MONT_REDC ? e.nprime : e.ninv << (32 - L);
   const uint32_t T0w = static_cast<uint32_t>(static_cast<int32_t>(T0));
-  // With the unsigned range the only good value is c itself, so the checks
-  // of a step fold into one word: the OR of r ^ c (one three-input logic
-  // operation per check), tested once per step.
-  constexpr bool kFold = (V == MONT_REDC && RK == kUnsigned);
+  // With the unsigned range (REDC) or the centred one (Algorithm 1) the only
+  // good value is the chain's c itself, so the checks of a step fold into
+  // one word: the OR of (r + off) ^ c (one three-input logic operation per
+  // check), tested once per step.  The folded chains are kept in [0, N):
+  // off = (N - 1) / 2 moves the centred range there.  Algorithm 1's own
+  // range (-N, N) has two good values, c and c - N (the latter for c > 0):
+  // with t = r + N, min(r, t) (unsigned) is r for r in [0, N) and r + N for
+  // r in [-N, 0), so it equals c exactly for the good values and for r = -N
+  // at c = 0, which the running minimum of t (zero only at r = -N) rules out.
+  constexpr bool kFoldWide = (V == MONT_SIGNED && RK == kWide);
+  constexpr bool kFold = (V == MONT_REDC && RK == kUnsigned) ||
+                         (V == MONT_SIGNED && RK == kCentred) || kFoldWide;
+  constexpr int kChainRK = kFold ? kUnsigned : RK;
+  const uint32_t off = (kFold && RK == kCentred) ? (N - 1u) / 2u : 0u;
   // W chains per step: the step's fixed cost (loop test, mismatch test,
   // branches) is shared by W checks.  Chain j >= 4 starts four steps of s
   // after chain j - 4; every chain steps by sW = W s mod N.  (Eight chains
-  // for the folded REDC check; Algorithm 1's wider check runs four, as eight
-  // cost it more registers than the shared step saves.)
+  // for the folded checks; the other range kinds run four, as eight cost
+  // them more registers than the shared step saves.)
   constexpr int W = kFold ? 8 : 4;
   uint32_t Tb[W], kb[W];
 #pragma unroll
@@ -245,9 +255,9 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
     kb[j] = Tb[j] * k;
   }
   uint32_t c[W];
-  c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;
+  c[0] = c0 + off; c[1] = c1 + off; c[2] = c2 + off; c[3] = c3 + off;
 #pragma unroll
-  for (int j = 4; j < W; ++j) c[j] = step_ref<RK>(c[j - 4], s4, N);
+  for (int j = 4; j < W; ++j) c[j] = step_ref<kChainRK>(c[j - 4], s4, N);
   uint32_t sW = s4;                                    // W s mod N, in [0, N)
 #pragma unroll
   for (int w = 4; w < W; w *= 2) sW = step_ref<kUnsigned>(sW, sW, N);
@@ -257,7 +267,7 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
   for (; i + W <= cnt; i += W) {
     int32_t r[W];
     bool g[W];
-    uint32_t diff = 0;
+    uint32_t diff = 0, tmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
       const uint32_t T = mad_lo(i, one, Tb[j]);
@@ -269,33 +279,40 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
         r[j] = (static_cast<int32_t>(T) >> L) -
                __mulhi(static_cast<int32_t>(u), static_cast<int32_t>(N));
       }
-      if constexpr (kFold) diff |= static_cast<uint32_t>(r[j]) ^ c[j];
-      else g[j] = fast_good<RK>(r[j], c[j], e);
+      if constexpr (kFoldWide) {
+        const uint32_t ru = static_cast<uint32_t>(r[j]), t = ru + N;
+        diff |= min(ru, t) ^ c[j];
+        tmin = min(tmin, t);
+      } else if constexpr (kFold) {
+        diff |= (static_cast<uint32_t>(r[j]) + off) ^ c[j];
+      } else {
+        g[j] = fast_good<RK>(r[j], c[j], e);
+      }
     }
     bool all_good = true;
     if constexpr (!kFold) {
 #pragma unroll
       for (int j = 0; j < W; ++j) all_good = all_good && g[j];
     }
-    if (kFold ? diff != 0u : !all_good) {
+    if (kFold ? (diff != 0u || tmin == 0u) : !all_good) {
       if constexpr (kFold) {   // the rare step with a mismatch: which checks
 #pragma unroll
-        for (int j = 0; j < W; ++j) g[j] = static_cast<uint32_t>(r[j]) == c[j];
+        for (int j = 0; j < W; ++j) g[j] = fast_good<RK>(r[j], c[j] - off, e);
       }
 #pragma unroll
       for (int j = 0; j < W; ++j) {
-        if (!g[j] && exact_bad(r[j], c[j], e)) {
+        if (!g[j] && exact_bad(r[j], c[j] - off, e)) {
           ++local;
           if (!full)
             full = record<kUnsignedTarget>(static_cast<int32_t>(T0w + i + static_cast<uint32_t>(j)),
-                                           r[j], c[j], N, cex, cex_n, cap);
+                                           r[j], c[j] - off, N, cex, cex_n, cap);
         }
       }
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-      if constexpr (RK == kCentred) {
-        c[j] = step_ref<RK>(c[j], sW, N);
+      if constexpr (kChainRK == kCentred) {
+        c[j] = step_ref<kChainRK>(c[j], sW, N);
       } else {
         c[j] = min(mad_lo(c[j], one, sW), mad_lo(c[j], one, sWm));
       }
@@ -304,11 +321,12 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
   for (; i < cnt; ++i) {
     const int32_t T = static_cast<int32_t>(T0w + i);
     const int32_t r = candidate<V, true>(T, e, p);
-    if (!fast_good<RK>(r, c[0], e) && exact_bad(r, c[0], e)) {
+    const uint32_t ct = c[0] - off;   // the chain in RK's representation
+    if (!fast_good<RK>(r, ct, e) && exact_bad(r, ct, e)) {
       ++local;
-      if (!full) full = record<kUnsignedTarget>(T, r, c[0], N, cex, cex_n, cap);
+      if (!full) full = record<kUnsignedTarget>(T, r, ct, N, cex, cex_n, cap);
     }
-    c[0] = step_ref<RK>(c[0], s1, N);
+    c[0] = step_ref<kChainRK>(c[0], s1, N);
   }
   return local;
 }
