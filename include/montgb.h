@@ -620,7 +620,7 @@ int mont_server_destroy(mont_server_t server);
  * only, never results.
  */
 typedef struct mont_launch_shape {
-  int threads;        /* threads per block: 64..512 (word kernels), 64, 128 or 256
+  int threads;        /* threads per block: 64..512 (word kernels), 32, 64, 128 or 256
                          (multi-limb), 128 or 256 (batched); multi-limb REDC reports 0
                          when untuned: the block size then follows the element count */
   int unroll;         /* 256-bit vectors in flight per thread per operand: 1, 2 or 4      */

@@ -392,7 +392,9 @@ int launch_multilimb_op(mont_ctx_t ctx, Mode mode, const void* x, const void* y,
   int team = shape.team > 0 ? shape.team : default_team(k);
   if (!team_supported(k, team)) team = default_team(k);
   int threads = shape.threads;
-  if (threads != 64 && threads != 128 && threads != 256) threads = default_threads(k, team, n);
+  if (threads != 32 && threads != 64 && threads != 128 && threads != 256) {
+    threads = default_threads(k, team, n);
+  }
   const int vec16 = aligned(x, 16) && aligned(out, 16) && (!y || aligned(y, 16)) ? 1 : 0;
   const cudaError_t e = dispatch(k, team, mode, sig, ctx->limb, static_cast<const uint32_t*>(x),
                                  static_cast<const uint32_t*>(y), static_cast<uint32_t*>(out), n,

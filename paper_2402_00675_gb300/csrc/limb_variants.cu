@@ -437,7 +437,8 @@ template <int K>
 cudaError_t launch_k(Mode mode, const LimbVarConst& c, const uint32_t* x, const uint32_t* y,
                      uint32_t* o, size_t n, cudaStream_t s, int vec16, const LaunchShape& shape) {
   const void* kern = reinterpret_cast<const void*>(limb_variant_kernel<K>);
-  const int threads = shape.threads == 256 ? 256 : 128;
+  const int threads =
+      shape.threads == 32 || shape.threads == 64 || shape.threads == 256 ? shape.threads : 128;
   int per_sm = resident_blocks(kern, threads);
   if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < per_sm) per_sm = shape.blocks_per_sm;
   const size_t want = (n + threads - 1) / threads;

@@ -106,7 +106,10 @@ bool shape_valid(int width, int mode, const LaunchShape& s) {
   if (mode == MONT_TUNE_MODE_BATCHED) {
     return (s.threads == 128 || s.threads == 256) && (s.unroll == 1 || s.unroll == 2 || s.unroll == 4);
   }
-  if (width > 64) return s.threads == 64 || s.threads == 128 || s.threads == 256;
+  if (width > 64) {
+    return (s.threads == 32 || s.threads == 64 || s.threads == 128 || s.threads == 256) &&
+           s.blocks_per_sm >= 0;
+  }
   return (s.threads == 64 || s.threads == 128 || s.threads == 256 || s.threads == 512) &&
          (s.unroll == 1 || s.unroll == 2 || s.unroll == 4) &&
          (s.vec_bytes == 0 || s.vec_bytes == 16 || s.vec_bytes == 32) && s.blocks_per_sm >= 0;
@@ -195,8 +198,9 @@ extern "C" int mont_autotune(mont_ctx_t ctx, size_t n, int flags, void* stream) 
           }
     } else if (ctx->variant != MONT_REDC && ctx->variant != MONT_SIGNED) {
       // Algorithms 2-4 at multi-limb widths: one thread per element, so the
-      // block size is the only choice
-      for (int th : {128, 256}) {
+      // block size is the only choice; small blocks spread a launch of a few
+      // warps per SM evenly over the SMs
+      for (int th : {32, 64, 128, 256}) {
         LaunchShape c;
         c.threads = th;
         cands.push_back(c);

@@ -250,9 +250,9 @@ def test_launch_shapes_do_not_change_results(k):
 
 
 def test_autotune_picks_a_block_size_and_keeps_results():
-    """mont_autotune on an Algorithm 2 context chooses between the two block
-    sizes (the kernel runs one thread per element: no lane teams); products
-    after tuning still equal the oracle's."""
+    """mont_autotune on an Algorithm 2 context chooses a block size (the
+    kernel runs one thread per element: no lane teams); products after tuning
+    still equal the oracle's."""
     k, variant = 8, mg.MONT_PLANTARD
     rnd = random.Random(600)
     l = 64 * k
@@ -261,7 +261,7 @@ def test_autotune_picks_a_block_size_and_keeps_results():
     try:
         mg.mont_autotune(ctx, 1 << 14)
         shape = mg.mont_tune_get(32 * k, variant, 0)
-        assert shape["threads"] in (128, 256) and shape["team"] == 0
+        assert shape["threads"] in (32, 64, 128, 256) and shape["team"] == 0
         cnt = 2000
         a, b = operands(variant, N, cnt, rnd), operands(variant, N, cnt, rnd)
         out = torch.zeros(cnt * k, dtype=torch.uint32, device="cuda")
