@@ -270,7 +270,11 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
     uint32_t diff = 0, tmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-      const uint32_t T = mad_lo(i, one, Tb[j]);
+      // Algorithm 1's signed high product is a half-rate multiply, which
+      // leaves the multiply pipe the busier one: its loop index and chain
+      // steps stay plain additions (ALU), only r + N goes to the multiply
+      // pipe; REDC's additions all go there
+      const uint32_t T = kFoldWide ? i + Tb[j] : mad_lo(i, one, Tb[j]);
       const uint32_t u = mad_lo(i, k, kb[j]);            // T k mod 2^32
       if constexpr (V == MONT_REDC) {
         const uint32_t t = mad_lo(u & mask, N, T) >> L;  // (T + mN) / R, below 2^32
@@ -280,7 +284,7 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
                __mulhi(static_cast<int32_t>(u), static_cast<int32_t>(N));
       }
       if constexpr (kFoldWide) {
-        const uint32_t ru = static_cast<uint32_t>(r[j]), t = ru + N;
+        const uint32_t ru = static_cast<uint32_t>(r[j]), t = mad_lo(N, one, ru);
         diff |= min(ru, t) ^ c[j];
         tmin = min(tmin, t);
       } else if constexpr (kFold) {
@@ -313,6 +317,8 @@ __device__ __forceinline__ uint32_t check_chunk_fast(int64_t T0, uint32_t cnt, c
     for (int j = 0; j < W; ++j) {
       if constexpr (kChainRK == kCentred) {
         c[j] = step_ref<kChainRK>(c[j], sW, N);
+      } else if constexpr (kFoldWide) {
+        c[j] = min(c[j] + sW, c[j] + sWm);
       } else {
         c[j] = min(mad_lo(c[j], one, sW), mad_lo(c[j], one, sWm));
       }

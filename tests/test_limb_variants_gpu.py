@@ -8,7 +8,9 @@ fixes).  Cases: every supported limb count; moduli at the variant's largest
 admissible size, random ones and ones with leading zero limbs; products,
 caller-supplied double-width T across the whole input domain, domain maps
 and their round trip; operands at the ends of their ranges; alpha on both
-sides of a limb boundary; in-place operation and misaligned buffers."""
+sides of a limb boundary; in-place operation and misaligned buffers; the
+benchmark's stated-size workloads, every element, at the built-in and the
+autotuned launch shape."""
 
 import random
 
@@ -271,3 +273,42 @@ def test_autotune_picks_a_block_size_and_keeps_results():
     finally:
         for mode in range(4):
             mg.mont_tune_set(32 * k, variant, mode, None)
+
+
+@pytest.mark.parametrize("bits,count", [(256, 1 << 21), (1024, 1 << 17), (2048, 1 << 15)])
+def test_full_size_workloads(bits, count):
+    """The benchmark's Algorithm 1-4 workloads at their stated sizes (the same
+    seeded moduli and operands), at the built-in launch shape and at the one
+    the autotuner picks for that size: every element against the whole-array
+    definition (Python integers)."""
+    from oracle import bulk
+    k = bits // 32
+    for variant in VARIANTS:
+        top_bits = {1: bits - 1, 2: bits - 1, 3: bits - 1, 4: bits - 2}[variant]
+        N = sy.random_odd_modulus(top_bits, seed=4 + variant)
+        l = log2R_of(variant, k)
+        ctx = mg.mont_ctx_create(N, l, variant, alpha=1, n_limbs=k)
+        a = sy.uniform_limb_residues(N, k, count, seed=40 + variant)
+        b = sy.uniform_limb_residues(N, k, count, seed=80 + variant)
+        signed = variant != mg.MONT_PLANTARD
+        if signed:
+            a, b = (sy.centred_limb_residues(N, x) for x in (a, b))
+        da, db = torch.from_numpy(a.reshape(-1)).cuda(), torch.from_numpy(b.reshape(-1)).cuda()
+        outs = []
+        try:
+            for tuned in (False, True):
+                if tuned:
+                    mg.mont_autotune(ctx, count)
+                out = torch.empty(count * k, dtype=torch.uint32, device="cuda")
+                mg.mont_mul(ctx, da, db, out, n=count)
+                torch.cuda.synchronize()
+                outs.append(out.cpu().numpy())
+        finally:
+            for mode in range(4):
+                mg.mont_tune_set(32 * k, variant, mode, None)
+        A, B = bulk.ints_from_limbs(a, k, signed), bulk.ints_from_limbs(b, k, signed)
+        want = bulk.mul_value_obj(variant, A, B, N, l, 1)
+        assert int(want[7]) == o.mul_value(variant, int(A[7]), int(B[7]), N, l, 1)
+        for tuned, got in zip((False, True), outs):
+            bad = np.flatnonzero(bulk.ints_from_limbs(got, k, signed) != want)
+            assert bad.size == 0, (bits, variant, tuned, bad[:5])
