@@ -221,6 +221,15 @@ def test_tune_table_set_get_without_gpu(L):
         mg.mont_tune_set(32, 1, 7, {"threads": 128})
     mg.mont_tune_set(32, 1, 0, None)
     assert mg.mont_tune_get(32, 1, 0)["threads"] == 256
+    # multi-limb widths: 32- to 256-thread blocks, blocks per SM >= 0
+    mg.mont_tune_set(1024, 0, 0, {"threads": 32, "team": 4, "blocks_per_sm": 3})
+    got = mg.mont_tune_get(1024, 0, 0)
+    assert (got["threads"], got["team"], got["blocks_per_sm"]) == (32, 4, 3)
+    for bad in ({"threads": 512}, {"threads": 128, "blocks_per_sm": -1}):
+        with pytest.raises(mg.MontError):
+            mg.mont_tune_set(1024, 0, 0, bad)
+    mg.mont_tune_set(1024, 0, 0, None)
+    assert mg.mont_tune_get(1024, 0, 0)["threads"] == 0
 
 
 def test_server_and_device_calls_fail_cleanly_without_gpu(L):

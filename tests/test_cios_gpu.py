@@ -131,8 +131,8 @@ def test_cios_ragged_misaligned_in_place(k):
 
 @pytest.mark.parametrize("k", [8, 32, 64])
 def test_cios_block_sizes_and_default_shape(k):
-    """64-, 128- and 256-thread blocks and the untuned size-dependent default
-    give the same products (several blocks and a ragged tail)."""
+    """32-, 64-, 128- and 256-thread blocks and the untuned size-dependent
+    default give the same products (several blocks and a ragged tail)."""
     rnd = random.Random(700 + k)
     N = moduli(k, rnd)[0]
     ctx = mg.mont_ctx_create(N, 32 * k, 0)
@@ -142,7 +142,7 @@ def test_cios_block_sizes_and_default_shape(k):
     want = [o.mul_value(0, x, y, N, 32 * k) for x, y in zip(a, b)]
     da, db = limbs_tensor(a, k), limbs_tensor(b, k)
     for team in TEAMS[k]:
-        for threads in (64, 128, 256):
+        for threads in (32, 64, 128, 256):
             for mode in range(4):
                 mg.mont_tune_set(32 * k, 0, mode, {"threads": threads, "team": team})
             out = torch.zeros(n * k, dtype=torch.uint32, device="cuda")

@@ -241,7 +241,8 @@ def test_launch_shapes_do_not_change_results(k):
     da, db = to_dev(a, k), to_dev(b, k)
     try:
         for shape in ({"threads": 128, "blocks_per_sm": 1}, {"threads": 256, "blocks_per_sm": 0},
-                      {"threads": 256, "blocks_per_sm": 3}, None):
+                      {"threads": 256, "blocks_per_sm": 3}, {"threads": 32, "blocks_per_sm": 0},
+                      {"threads": 64, "blocks_per_sm": 2}, None):
             mg.mont_tune_set(32 * k, variant, 0, shape)
             out = torch.zeros(cnt * k, dtype=torch.uint32, device="cuda")
             mg.mont_mul(ctx, da, db, out, n=cnt)
