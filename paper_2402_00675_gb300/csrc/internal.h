@@ -83,6 +83,39 @@ cudaError_t launch_limb_variant(int k, Mode mode, const LimbVarConst& c, const u
                                 const uint32_t* y, uint32_t* o, size_t n, cudaStream_t s,
                                 int vec16, const LaunchShape& shape);
 
+// Launch a kernel with programmatic stream serialization: it may be
+// scheduled while the kernel before it in the stream drains.  The kernel must
+// execute `griddepcontrol.wait` before its first memory access (and may then
+// execute `griddepcontrol.launch_dependents`).  Used for the HBM-bound word
+// kernels only: blocks scheduled early land in whatever slots the previous
+// grid frees, unevenly over the SMs, which a bandwidth-bound kernel does not
+// notice but a compute-bound grid-stride kernel does (the multi-limb REDC
+// kernel at 1024 bits measured 57 -> 63-76 us with it).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned threads, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// The first statements of a kernel launched by launch_pdl: wait for the
+// kernel before it, then let the next one's blocks be scheduled into slots
+// this grid frees (a dependent kernel is scheduled only once every block of
+// this grid has started, so it never holds slots this grid still needs).
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 // Number of SMs of the current device (cached per device).
 int device_sm_count();
 

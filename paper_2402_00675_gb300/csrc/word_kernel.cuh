@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(512) word_kernel(const void* __restrict__ xp,
                                                    const typename Op::C c) {
   using E = typename Op::E;
   using TT = typename Op::TT;
+  pdl_enter();   // launched by launch_pdl (without its attribute, a no-op)
   const size_t nthreads = static_cast<size_t>(gridDim.x) * blockDim.x;
   const size_t tid = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   size_t done = 0;
@@ -187,8 +188,7 @@ cudaError_t launch_one(const typename Op::C& c, const void* x, const void* y, vo
   const int per_sm = shape.blocks_per_sm > 0 ? shape.blocks_per_sm : resident_blocks(reinterpret_cast<const void*>(kernel), threads);
   const size_t cap = static_cast<size_t>(device_sm_count()) * per_sm;
   const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
-  kernel<<<grid, threads, 0, s>>>(x, y, out, n, c);
-  return cudaGetLastError();
+  return launch_pdl(kernel, grid, static_cast<unsigned>(threads), 0, s, x, y, out, n, c);
 }
 
 template <class Op, Mode M>
