@@ -55,7 +55,7 @@ ALPHA = 1
 # full-size launch.  Reads equal the algorithmic 536.9 MB; writes (228.1 MB of
 # 268.4 MB) exclude the output tail still dirty in L2 when the kernel ends,
 # which the next launch writes back.
-NCU_TRAFFIC_BYTES_PER_LAUNCH = 764974976
+NCU_TRAFFIC_BYTES_PER_LAUNCH = 764626656
 
 
 def parse_args():
