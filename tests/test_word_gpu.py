@@ -205,3 +205,48 @@ def test_full_size_word32_variants_2p26(N):
         assert got.min() >= lo and got.max() <= hi
         for i in (0, n - 1):
             assert int(want[i]) == o.mul_value(variant, int(xa[i]), int(xb[i]), N, l, 1)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_dependent_launch_chain(variant, width):
+    """Word kernels start while the kernel before them drains (programmatic
+    launch) and wait for it before touching memory.  A chain of 8 dependent
+    products x <- x b, ping-ponging between two buffers (each launch reads
+    what the previous one wrote and overwrites what it read), run directly
+    and replayed from a captured CUDA graph, equals the oracle's chain."""
+    rnd = random.Random(4000 + 10 * variant + width)
+    l = log2R_of(variant, width)
+    dt = np_dtype(variant, width)
+    N = moduli_for(variant, width, rnd)[-1]
+    ctx = mg.mont_ctx_create(N, l, variant, alpha=1)
+    n = (1 << 18) + 3
+    a = operands(variant, N, n, rnd)
+    b = operands(variant, N, n, rnd)
+    want = np.array(a, dtype=object)
+    B = np.array(b, dtype=object)
+    for _ in range(8):
+        want = bulk.mul_value_obj(variant, want, B, N, l, 1)
+    db = dev(b, dt)
+    bufs = [dev(a, dt), empty_like_elems(n, dt)]
+
+    def chain():
+        for i in range(8):
+            mg.mont_mul(ctx, bufs[i % 2], db, bufs[(i + 1) % 2], n=n)
+
+    chain()
+    sync()
+    assert host(bufs[0]) == [int(x) for x in want]
+    bufs[0].copy_(dev(a, dt))
+    bufs[1].zero_()
+    sync()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        chain()
+    torch.cuda.current_stream().wait_stream(side)
+    bufs[0].copy_(dev(a, dt))   # capture does not run the kernels; start again
+    g.replay()
+    sync()
+    assert host(bufs[0]) == [int(x) for x in want]
